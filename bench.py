@@ -1,0 +1,546 @@
+#!/usr/bin/env python
+"""Benchmark of the batched hash-table path on GB300.
+
+Default workload (one JSON line): four 2^28-slot tables -- DoubleHT,
+DoubleHT(M), P2HT, P2HT(M), paper-default bucket and tile sizes -- each
+prefilled to 0.85 load outside the timed region.  One step, per table:
+  insert a 5% slice of new keys (0.85 -> 0.90 load), query 2^24 present keys,
+  query 2^24 absent keys, upsert-add 2^24 present keys (values in [1, 1000]),
+  erase the slice again (0.90 -> 0.85), read the live count.
+``value`` = all ops of all tables / device time of K steps (Gops/s); ``e2e``
+times the same steps through the C ABI with pinned host buffers (copies in).
+
+--impl reference: the CPU oracle (the map definition, single thread) on a
+bounded sample of the same step; ``--sweep`` writes the load/tile sweep.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+DESIGNS = [("double", False, "DoubleHT"), ("double", True, "DoubleHT(M)"), ("p2", False, "P2HT"),
+           ("p2", True, "P2HT(M)")]
+METRIC = "Gops/s insert/query/upsert at 0.9 load; % of HBM roofline; serve p50/p99 latency"
+UNIT = "Gops/s"
+PHASES = ["insert", "query_pos", "query_neg", "upsert_add", "erase"]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--log2-slots", type=int, default=28)
+    p.add_argument("--load", type=float, default=0.9)
+    p.add_argument("--nq", type=int, default=1 << 24, help="queries / upserts per phase")
+    p.add_argument("--designs", default="all")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--sweep", default="", help="write the load/tile sweep as JSON lines to this file")
+    p.add_argument("--sweep-log2-slots", default="28,22")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+def to_dev(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(dev, non_blocking=False)
+
+
+def gen_dev(seed, n, start, dev, chunk=1 << 24):
+    """The splitmix64 key stream (positions start .. start+n-1) on the device."""
+    import torch
+    out = torch.empty(n, dtype=torch.int64, device=dev)
+    for off in range(0, n, chunk):
+        m = min(chunk, n - off)
+        k = W.splitmix64(seed, m, start + off)
+        if ((k == np.uint64(0)) | (k >= np.uint64((1 << 64) - 2))).any():
+            raise RuntimeError("sentinel drawn from the key stream; pick another seed")
+        out[off:off + m].copy_(torch.from_numpy(k.view(np.int64)))
+    return out
+
+
+def peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def recorded_traffic():
+    """Per-launch DRAM traffic of the dominant kernel from a committed ncu summary."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+# ---------------------------------------------------------------------------
+def bench_ours(args, rank, world):
+    import torch
+    import paper_2509_16407_gb300 as ws
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    S = 1 << args.log2_slots
+    base_n = int(0.85 * S)
+    top_n = int(args.load * S)
+    slice_n = top_n - base_n
+    nq = args.nq
+    designs = DESIGNS if args.designs == "all" else [d for d in DESIGNS if d[2] in args.designs.split(",")]
+    seed = 0x5EED + 7919 * rank
+
+    # device-resident inputs (one key stream: base | slice | absent)
+    keys_base = gen_dev(seed, base_n, 0, dev)
+    keys_slice = gen_dev(seed, slice_n, base_n, dev)
+    keys_neg = gen_dev(seed, nq, top_n, dev)
+    vals_base = keys_base * 3
+    vals_slice = keys_slice * 3
+    pos_idx = torch.from_numpy((W.splitmix64(seed + 1, nq) % np.uint64(top_n)).astype(np.int64)).to(dev)
+    allk = torch.cat([keys_base, keys_slice])
+    keys_pos = allk[pos_idx].contiguous()
+    del allk
+    up_idx = torch.from_numpy((W.splitmix64(seed + 2, nq) % np.uint64(base_n)).astype(np.int64)).to(dev)
+    keys_up = keys_base[up_idx].contiguous()
+    vals_up = torch.from_numpy(W.uniform_int(seed + 3, nq, 1, 1000).view(np.int64)).to(dev)
+    out_q = torch.empty(nq, dtype=torch.int64, device=dev)
+
+    tables = []
+    for scheme, meta, name in designs:
+        t = ws.Table(S, scheme, meta)
+        t.insert(keys_base, vals_base)
+        torch.cuda.synchronize()
+        assert t.count() == base_n, (name, t.count())
+        assert t.last_error()["status"] == 0, name
+        tables.append((name, t))
+
+    stream = torch.cuda.current_stream(dev)
+
+    def step(evs=None):
+        for di, (name, t) in enumerate(tables):
+            if evs is not None:
+                evs[di][0].record(stream)
+            t.insert(keys_slice, vals_slice)
+            if evs is not None:
+                evs[di][1].record(stream)
+            t.query(keys_pos, out=out_q)
+            if evs is not None:
+                evs[di][2].record(stream)
+            t.query(keys_neg, out=out_q)
+            if evs is not None:
+                evs[di][3].record(stream)
+            t.upsert(keys_up, vals_up, op="add")
+            if evs is not None:
+                evs[di][4].record(stream)
+            t.erase(keys_slice)
+            if evs is not None:
+                evs[di][5].record(stream)
+        for name, t in tables:
+            c = t.count()
+            if c != base_n:
+                raise RuntimeError(f"{name}: count {c} != {base_n} after a step")
+
+    ops_per_table = 2 * slice_n + 3 * nq
+    ops_per_step = ops_per_table * len(tables)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # probe costs (lines / sectors per op) measured on the live tables, untimed
+    sample = 1 << 20
+    costs = {}
+    for name, t in tables:
+        c = {}
+        cs, _ = t.probe_cost(keys_slice[:sample])  # insert scan cost at 0.85 load
+        c["insert"] = cs
+        t.insert(keys_slice, vals_slice)
+        c["query_pos"], _ = t.probe_cost(keys_pos[:sample])
+        c["query_neg"], _ = t.probe_cost(keys_neg[:sample])
+        c["upsert_add"], _ = t.probe_cost(keys_up[:sample])
+        c["erase"], _ = t.probe_cost(keys_slice[:sample])
+        t.erase(keys_slice)
+        torch.cuda.synchronize()
+        costs[name] = {}
+        for ph, v in c.items():
+            v = v.cpu().numpy().view(np.uint64)
+            costs[name][ph] = {"sectors": float((v & np.uint64(0xFFFFFFFF)).mean()),
+                               "lines": float((v >> np.uint64(32)).mean())}
+
+    meta_of = {d[2]: d[1] for d in designs}
+
+    def alg_bytes(name, ph):
+        sec = costs[name][ph]["sectors"] * 32.0
+        m = meta_of[name]
+        if ph == "insert":      # scan + written slot sector (+ tag sector) + key, value in
+            return sec + 32 + (32 if m else 0) + 16
+        if ph in ("query_pos", "query_neg"):  # scan + key in, value out
+            return sec + 16
+        if ph == "upsert_add":  # scan + value sector write-back + key, value in
+            return sec + 32 + 16
+        return sec + 32 + (32 if m else 0) + 8  # erase: scan + slot (+ tag) write + key in
+
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in tables] for _ in range(args.steps)]
+    clk = ClockSampler(dev.index if dev.index is not None else 0)
+    clk.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    ms = t0.elapsed_time(t1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    total_ops = ops_per_step * args.steps * world
+    value = total_ops / (ms * 1e-3) / 1e9
+
+    # per-phase times, achieved bandwidth and probe costs
+    peak, peak_kind = peak_gbs()
+    phase_ms = {name: {ph: 0.0 for ph in PHASES} for name, _ in tables}
+    for k in range(args.steps):
+        for di, (name, _) in enumerate(tables):
+            for pi, ph in enumerate(PHASES):
+                phase_ms[name][ph] += evs[k][di][pi].elapsed_time(evs[k][di][pi + 1])
+    n_of = {"insert": slice_n, "query_pos": nq, "query_neg": nq, "upsert_add": nq, "erase": slice_n}
+    breakdown = {}
+    dom = None
+    for name, _ in tables:
+        breakdown[name] = {}
+        for ph in PHASES:
+            per_launch_ms = phase_ms[name][ph] / args.steps
+            b = alg_bytes(name, ph)
+            gbs = b * n_of[ph] / (per_launch_ms * 1e-3) / 1e9
+            breakdown[name][ph] = {
+                "gops": round(n_of[ph] / (per_launch_ms * 1e-3) / 1e9, 3),
+                "ms": round(per_launch_ms, 4),
+                "alg_bytes_per_op": round(b, 1),
+                "lines_per_op": round(costs[name][ph]["lines"], 3),
+                "sectors_per_op": round(costs[name][ph]["sectors"], 3),
+                "achieved_gbs": round(gbs, 1),
+                "frac_of_measured_hbm": round(gbs / peak, 4),
+            }
+            if dom is None or per_launch_ms > dom[2]:
+                dom = (name, ph, per_launch_ms, gbs, b * n_of[ph])
+    kernel_names = {"insert": "batch_kernel<KIND_UPSERT, op=insert>", "query_pos": "batch_kernel<KIND_QUERY>",
+                    "query_neg": "batch_kernel<KIND_QUERY>", "upsert_add": "batch_kernel<KIND_UPSERT, op=add>",
+                    "erase": "batch_kernel<KIND_ERASE>"}
+    tr = recorded_traffic()
+    dom_key = f"{dom[0]}:{dom[1]}"
+    traffic = tr.get(dom_key, {}).get("dram_bytes_per_launch") if tr.get("valid_for_commit") else None
+    roofline = {"bound": "hbm", "achieved": round(dom[3], 1), "peak": peak, "unit": "GB/s",
+                "frac": round(dom[3] / peak, 4), "traffic": traffic,
+                "kernel": f"{dom[0]} {dom[1]}: {kernel_names[dom[1]]}",
+                "alg_bytes_per_launch": int(dom[4]), "peak_kind": f"{peak_kind} (burst copy)"}
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e = bench_e2e(args, tables, keys_slice, vals_slice, keys_pos, keys_neg, keys_up, vals_up, base_n,
+                        ops_per_step, world, dev)
+
+    launches = args.steps * len(tables) * len(PHASES)
+    result = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {
+            "workload": f"2^{args.log2_slots}-slot tables at {args.load} load (0.85 -> {args.load} slice insert,"
+                        f" 2^{int(np.log2(nq))} positive + negative queries, 2^{int(np.log2(nq))} upsert-add,"
+                        f" slice erase, count), designs {[d[2] for d in designs]}",
+            "slots": S, "load": args.load, "base_keys": base_n, "slice_keys": slice_n, "queries": nq,
+            "ops_per_step": ops_per_step * world,
+            "tiles": {d[2]: t.info()["tile"] for d, (_, t) in zip(designs, tables)},
+            "bucket_slots": {d[2]: t.info()["bucket_slots"] for d, (_, t) in zip(designs, tables)},
+            "l2": "inputs larger than L2, no flush: each table (4-4.5 GiB, 33x the 129 MB L2) is probed at"
+                  " random; query/upsert key arrays are 134 MB",
+            "parallelism": f"replicas x{world}",
+        },
+        "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "breakdown": breakdown,
+    }
+    return result
+
+
+def bench_e2e(args, tables, keys_slice, vals_slice, keys_pos, keys_neg, keys_up, vals_up, base_n, ops_per_step,
+              world, dev):
+    """Same steps through the C ABI with pinned host inputs and outputs."""
+    import torch
+    h = {n: x.cpu().pin_memory() for n, x in (("ks", keys_slice), ("vs", vals_slice), ("kp", keys_pos),
+                                              ("kn", keys_neg), ("ku", keys_up), ("vu", vals_up))}
+    out_host = torch.empty(keys_pos.numel(), dtype=torch.int64).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for name, t in tables:
+            t.insert(h["ks"], h["vs"])
+            t.query(h["kp"], out=out_host)
+            t.query(h["kn"], out=out_host)
+            t.upsert(h["ku"], h["vu"], op="add")
+            t.erase(h["ks"])
+        for name, t in tables:
+            if t.count() != base_n:
+                raise RuntimeError("e2e count mismatch")
+
+    step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    n_t = len(tables)
+    h2d = n_t * (keys_slice.numel() * 16 + keys_pos.numel() * 8 + keys_neg.numel() * 8 + keys_up.numel() * 16
+                 + keys_slice.numel() * 8)
+    d2h = n_t * (keys_pos.numel() * 8 + keys_neg.numel() * 8)
+    return {"value": round(ops_per_step * args.steps * world / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_step_sample(log2_slots=22, load=0.9, nq=1 << 18, seed=0xC0FFEE):
+    """One step of the same workload shape at 2^log2_slots slots, on the oracle.
+    Returns (ops, seconds) for one step (prefill untimed), plus a runner."""
+    import oracle
+    S = 1 << log2_slots
+    base_n = int(0.85 * S)
+    top_n = int(load * S)
+    slice_n = top_n - base_n
+    ks = W.distinct_keys(seed, top_n + nq)
+    base, slc, neg = ks[:base_n], ks[base_n:top_n], ks[top_n:]
+    with np.errstate(over="ignore"):
+        vb, vs = base * np.uint64(3), slc * np.uint64(3)
+    pos = ks[:top_n][W.splitmix64(seed + 1, nq) % np.uint64(top_n)]
+    up = base[W.splitmix64(seed + 2, nq) % np.uint64(base_n)]
+    vu = W.uniform_int(seed + 3, nq, 1, 1000)
+    om = oracle.OracleMap()
+    om.insert(base, vb)
+
+    def run():
+        t0 = time.perf_counter()
+        om.insert(slc, vs)
+        om.query(pos)
+        om.query(neg)
+        om.upsert(up, vu, 0)
+        om.erase(slc)
+        dt = time.perf_counter() - t0
+        assert om.count() == base_n
+        return dt
+
+    return 2 * slice_n + 3 * nq, run, f"2^{log2_slots}-slot-equivalent map at 0.85->{load} load, {2 * slice_n + 3 * nq} ops/step"
+
+
+def cpu_baseline(seconds=10.0):
+    ops, run, desc = oracle_step_sample()
+    done, spent = 0, 0.0
+    while spent < seconds:
+        spent += run()
+        done += ops
+    return {"value": round(done / spent / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{desc}; {done} ops in {spent:.1f} s (single-threaded std::unordered_map)"}
+
+
+def bench_reference(args, rank, world):
+    if rank != 0:
+        return None
+    ops, run, desc = oracle_step_sample()
+    for _ in range(args.warmup):
+        run()
+    spent = 0.0
+    for _ in range(args.steps):
+        spent += run()
+    value = ops * args.steps / spent / 1e9
+    return {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(spent / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": desc, "parallelism": "1 host thread"},
+            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ---------------------------------------------------------------------------
+# load / tile sweep (config 2): one JSON line per (slots, design, tile, load)
+# ---------------------------------------------------------------------------
+def sweep(args):
+    import torch
+    import paper_2509_16407_gb300 as ws
+    dev = torch.device("cuda", 0)
+    peak, _ = peak_gbs()
+    out = open(args.sweep, "w")
+    loads = [0.5, 0.7, 0.8, 0.9, 0.95]
+    for lg in [int(x) for x in args.sweep_log2_slots.split(",")]:
+        S = 1 << lg
+        nq = min(1 << 24, S // 4)
+        top = int(0.95 * S)
+        keys = gen_dev(0xABC + lg, top + nq, 0, dev)
+        vals = keys * 3
+        neg = keys[top:]
+        for scheme, meta, name in DESIGNS:
+            for tile in (4, 8, 16, 32):
+                t = ws.Table(S, scheme, meta, tile=tile)
+                have = 0
+                for lf in loads:
+                    n_lf = int(lf * S)
+                    lo = int((lf - 0.05) * S)
+                    # fill to lf - 0.05 untimed, then time the 5% slice
+                    if lo > have:
+                        t.insert(keys[have:lo], vals[have:lo])
+                    a, b, c, d, e = (torch.cuda.Event(enable_timing=True) for _ in range(5))
+                    a.record()
+                    st = t.insert(keys[lo:n_lf], vals[lo:n_lf], return_status=True)
+                    b.record()
+                    pos = keys[:n_lf][torch.randint(0, n_lf, (nq,), device=dev,
+                                                    generator=torch.Generator(device=dev).manual_seed(lg))]
+                    c.record()
+                    t.query(pos)
+                    d.record()
+                    t.query(neg)
+                    e.record()
+                    torch.cuda.synchronize()
+                    have = n_lf
+                    fails = int((st == ws.FAIL_FULL).sum().item())
+                    pc, _ = t.probe_cost(pos[: 1 << 18])
+                    nc, _ = t.probe_cost(neg[: 1 << 18])
+                    pcs = float((pc.cpu().numpy().view(np.uint64) & np.uint64(0xFFFFFFFF)).mean())
+                    ncs = float((nc.cpu().numpy().view(np.uint64) & np.uint64(0xFFFFFFFF)).mean())
+                    ins_ms, qp_ms, qn_ms = a.elapsed_time(b), c.elapsed_time(d), d.elapsed_time(e)
+                    rec = {"slots": S, "design": name, "tile": tile, "load": lf,
+                           "insert_gops": round((n_lf - lo) / ins_ms / 1e6, 3),
+                           "query_pos_gops": round(nq / qp_ms / 1e6, 3),
+                           "query_neg_gops": round(nq / qn_ms / 1e6, 3),
+                           "query_pos_gbs": round(nq * (pcs * 32 + 16) / qp_ms / 1e6, 1),
+                           "query_neg_gbs": round(nq * (ncs * 32 + 16) / qn_ms / 1e6, 1),
+                           "query_pos_sectors": round(pcs, 3), "query_neg_sectors": round(ncs, 3),
+                           "insert_failures": fails, "peak_gbs": peak}
+                    out.write(json.dumps(rec) + "\n")
+                    out.flush()
+                t.close()
+                torch.cuda.empty_cache()
+    out.close()
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        res = bench_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    if args.sweep:
+        sweep(args)
+        return
+    res = bench_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu:
+            res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

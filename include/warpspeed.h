@@ -1,0 +1,211 @@
+/*
+ * warpspeed.h -- C ABI of a GB300-native (sm_103a) batched concurrent hash table.
+ *
+ * The operations follow the API of WarpSpeed (Pandey et al., arXiv 2509.16407),
+ * §5.1 "Hash table API":
+ *   Upsert(key, value, callback): insert the pair if the key is absent, otherwise
+ *     run the callback on the stored value.  The empty callback is
+ *     insert-if-unique; the atomicAdd callback accumulates.
+ *   Query(key, &value): true and the value if the key is present.
+ *   Erase(key): true if the key was present (and removes it); otherwise the
+ *     table is unchanged.
+ * Table designs (§2.2, §5): double hashing over 8-slot buckets (DoubleHT) and
+ * power-of-two-choice over 32-slot buckets (P2HT), each optionally with a
+ * 16-bit fingerprint per slot (the "(M)" metadata variants, §4.3).  Same-key
+ * writers serialise on one lock bit of the key's primary bucket, held in an
+ * external array (§4.1, §5 "Concurrency and metadata"); queries take no lock
+ * and read each slot with one 128-bit load (§4.2).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Keys and values are uint64_t.  Keys 0 (EMPTY), 2^64-1 (TOMBSTONE) and
+ *  2^64-2 (RESERVED) are sentinels: ops on them get the per-op status
+ *  WS_FAIL_BADKEY and change nothing.
+ *
+ *  Batch buffers (keys, vals, ops, outputs) may be DEVICE pointers on the
+ *  table's device (the fast path: kernels read them in place) or HOST pointers
+ *  (pinned or pageable): the library then streams them through internal device
+ *  staging buffers in chunks, overlapping copies with the kernels, and the
+ *  outputs land in host memory once `stream` completes.  Buffers must be
+ *  8-byte aligned (u64 arrays) and stay valid until `stream` completes.  The
+ *  caller owns all batch buffers; the table owns its slot, tag, lock and
+ *  staging memory and frees it in ws_destroy().
+ *
+ *  Every batch call is asynchronous on `stream` (a cudaStream_t; NULL = the
+ *  legacy default stream).  One call is one phase: ops inside a call run
+ *  concurrently; calls on one table must be ordered (same stream, or the
+ *  caller synchronises).  Inside one call, queries observe the state at the
+ *  start of the call for every key the call does not also write; for a
+ *  mixed batch the keys of its query, erase and upsert classes must be
+ *  disjoint (any overlap still leaves a valid linearisation for queries, but
+ *  an erase and an upsert of one key in one batch is outside the contract).
+ *
+ *  Return value: argument and launch errors are reported immediately.
+ *  Per-op failures (no free slot, lock timeout, sentinel key) do not fail
+ *  the call: they are written to the optional per-op status array and
+ *  counted in the table's device error counters (ws_last_error).
+ *
+ * Per-op status codes (uint8_t): WS_MISS 0, WS_FOUND 1, WS_INSERTED 2,
+ *  WS_FAIL_FULL 3, WS_FAIL_BADKEY 4 (also an unknown mixed op code),
+ *  WS_FAIL_TIMEOUT 5.
+ */
+#ifndef WARPSPEED_H
+#define WARPSPEED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ws_table ws_table;       /* opaque; owned by the library */
+typedef struct CUstream_st* ws_stream;  /* identical to cudaStream_t */
+
+typedef enum { WS_DOUBLE = 0, WS_P2 = 1 } ws_scheme;
+
+/* Upsert callbacks of §5.1: ADD = atomicAdd (wrapping mod 2^64), MAX = u64 max,
+ * REPLACE = overwrite, INSERT = the empty callback (insert-if-unique). */
+typedef enum { WS_OP_ADD = 0, WS_OP_MAX = 1, WS_OP_REPLACE = 2, WS_OP_INSERT = 3 } ws_upsert_op;
+
+/* Op codes of a mixed batch (ws_mixed). */
+typedef enum {
+  WS_MX_QUERY = 0, WS_MX_INSERT = 1, WS_MX_ADD = 2, WS_MX_MAX = 3, WS_MX_REPLACE = 4, WS_MX_ERASE = 5
+} ws_mixed_op;
+
+typedef enum {
+  WS_OK = 0,
+  WS_ERR_INVALID = 1,      /* bad argument (null table, bad size, misaligned, wrong device) */
+  WS_ERR_INVALID_KEY = 2,  /* (ws_last_error) some op named a sentinel key */
+  WS_ERR_OOM = 3,          /* device allocation failed */
+  WS_ERR_FULL = 4,         /* (ws_last_error) some insert found no free slot */
+  WS_ERR_TIMEOUT = 5,      /* (ws_last_error) some op hit the lock spin limit */
+  WS_ERR_CUDA = 6          /* a CUDA call failed; see ws_cuda_error_string() */
+} ws_status;
+
+enum { WS_MISS = 0, WS_FOUND = 1, WS_INSERTED = 2, WS_FAIL_FULL = 3, WS_FAIL_BADKEY = 4,
+       WS_FAIL_TIMEOUT = 5 };
+
+/* Full configuration; ws_table_create() fills the paper's defaults (§5):
+ *  DoubleHT: 8-slot buckets (one 128-byte line), tile 8; DoubleHT(M): 32-slot
+ *  buckets, tile 4; P2HT: 32-slot buckets (four lines), tile 8; P2HT(M): 32,
+ *  tile 4.  bucket_slots in {8, 16, 32} (32 when metadata != 0); tile in
+ *  {4, 8, 16, 32}.  max_probe = number of buckets a double-hashing probe
+ *  sequence may visit (default 80, clamped to the bucket count); ignored by P2.
+ *  The bucket count is capacity / bucket_slots rounded up to a power of two. */
+typedef struct {
+  uint64_t capacity;
+  int32_t scheme;        /* ws_scheme */
+  int32_t metadata;      /* 0 or 1 */
+  int32_t bucket_slots;  /* 0 = default */
+  int32_t tile;          /* 0 = default */
+  uint32_t max_probe;    /* 0 = default (80) */
+  uint32_t spin_limit;   /* lock acquisition attempts before WS_FAIL_TIMEOUT; 0 = default */
+  int32_t device;        /* -1 = current device */
+  int32_t reserved;
+} ws_config;
+
+typedef struct {
+  uint64_t slots;         /* total slots S = buckets * bucket_slots */
+  uint64_t buckets;       /* nb (power of two) */
+  uint64_t bucket_slots;  /* B */
+  uint64_t tile;          /* T */
+  uint64_t max_probe;     /* effective probe limit in buckets */
+  uint64_t seed1, seed2;  /* hash seeds of h1, h2 */
+  uint64_t bytes;         /* device bytes owned (slots + tags + locks + counters) */
+  int32_t scheme, metadata, device, never_erased;
+} ws_table_info;
+
+/* Create a table.  Slots start EMPTY.  Returns WS_ERR_OOM if device memory is
+ * short (nothing is leaked), WS_ERR_INVALID for a bad configuration. */
+ws_status ws_table_create(uint64_t capacity, ws_scheme scheme, int metadata, ws_table** out);
+ws_status ws_table_create_ex(const ws_config* cfg, ws_table** out);
+/* Frees all device memory of the table; synchronises the device first. */
+ws_status ws_destroy(ws_table* t);
+ws_status ws_table_info_get(const ws_table* t, ws_table_info* out);
+/* Reset every slot to EMPTY (asynchronous on stream); counters are zeroed. */
+ws_status ws_clear(ws_table* t, ws_stream stream);
+/* Change the tile size used by later calls (4, 8, 16 or 32). */
+ws_status ws_set_tile(ws_table* t, int tile);
+ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
+
+/* Insert-if-unique (§5.1 Upsert with the empty callback).  status_out: per-op
+ * WS_INSERTED / WS_FOUND (already present, value kept) / WS_FAIL_*; nullable. */
+ws_status ws_insert(ws_table* t, const uint64_t* keys, const uint64_t* vals, uint64_t n,
+                    ws_stream stream);
+ws_status ws_insert_ex(ws_table* t, const uint64_t* keys, const uint64_t* vals, uint64_t n,
+                       uint8_t* status_out, ws_stream stream);
+
+/* Upsert with callback op (§5.1).  Absent keys are inserted with their value;
+ * present keys get the callback.  Duplicate keys in one batch: ADD and MAX
+ * results are exact; REPLACE leaves one of the given values. */
+ws_status ws_upsert(ws_table* t, const uint64_t* keys, const uint64_t* vals, uint64_t n,
+                    ws_upsert_op op, ws_stream stream);
+ws_status ws_upsert_ex(ws_table* t, const uint64_t* keys, const uint64_t* vals, uint64_t n,
+                       ws_upsert_op op, uint8_t* status_out, ws_stream stream);
+
+/* Query (§5.1).  vals_out[i] = value, or 0 on a miss; found_out (nullable) gets
+ * the per-op status (WS_FOUND / WS_MISS / WS_FAIL_BADKEY).  Lock-free. */
+ws_status ws_query(ws_table* t, const uint64_t* keys, uint64_t* vals_out, uint64_t n,
+                   ws_stream stream);
+ws_status ws_query_ex(ws_table* t, const uint64_t* keys, uint64_t* vals_out, uint8_t* found_out,
+                      uint64_t n, ws_stream stream);
+
+/* Erase (§5.1).  vals_out (nullable) gets the removed value (0 on a miss);
+ * status_out (nullable) WS_FOUND / WS_MISS.  Duplicate keys in one batch:
+ * exactly one reports WS_FOUND. */
+ws_status ws_erase(ws_table* t, const uint64_t* keys, uint64_t* vals_out, uint64_t n,
+                   ws_stream stream);
+ws_status ws_erase_ex(ws_table* t, const uint64_t* keys, uint64_t* vals_out, uint8_t* status_out,
+                      uint64_t n, ws_stream stream);
+
+/* One kernel over an op-coded batch (ws_mixed_op per element), as in the
+ * paper's aging benchmark where inserts, queries and removals of an iteration
+ * run in one kernel (§6.4).  vals may be NULL when no op needs a value;
+ * vals_out (nullable) gets query values / erased values (0 otherwise). */
+ws_status ws_mixed(ws_table* t, const uint8_t* ops, const uint64_t* keys, const uint64_t* vals,
+                   uint64_t* vals_out, uint8_t* status_out, uint64_t n, ws_stream stream);
+
+/* Probe-count instrumentation (§5 "probe count", Table 1): for each key, the
+ * memory a query of it touches on the current table, without changing the
+ * table.  cost_out[i] = (cache lines << 32) | (32-byte DRAM sectors), counting
+ * every bucket step (T slots of 16 B) and, with metadata, every 64-byte tag
+ * read (2 sectors, 1 line) and every candidate slot read (1 sector, 1 line).
+ * found_out (nullable) as in ws_query_ex.  Asynchronous on stream. */
+ws_status ws_probe_cost(ws_table* t, const uint64_t* keys, uint64_t* cost_out, uint8_t* found_out, uint64_t n,
+                        ws_stream stream);
+
+/* Number of live keys.  Synchronises the table's last stream. */
+ws_status ws_count(ws_table* t, uint64_t* out);
+
+/* Per-op failure counters accumulated since creation/clear (synchronising).
+ * Returns WS_OK if all are zero, else the most severe of WS_ERR_TIMEOUT,
+ * WS_ERR_FULL, WS_ERR_INVALID_KEY.  Any pointer may be NULL. */
+ws_status ws_last_error(ws_table* t, uint64_t* n_full, uint64_t* n_timeout, uint64_t* n_badkey);
+
+/* Adversarial-benchmark hooks (§4.1): the bucket count, and each key's
+ * primary bucket computed on the device (out: device or host u64[n]). */
+ws_status ws_num_buckets(const ws_table* t, uint64_t* out);
+ws_status ws_primary_bucket(ws_table* t, const uint64_t* keys, uint64_t* out, uint64_t n,
+                            ws_stream stream);
+
+/* Copy the slot array (S x {key, val}, 16 B each) and, for metadata tables,
+ * the tag array (S x u16) to host memory.  Synchronising.  host_tags may be
+ * NULL.  For layout checks and snapshots. */
+ws_status ws_dump(ws_table* t, void* host_slots, void* host_tags);
+
+/* Fault injection from the host: set (locked != 0) or clear every lock bit
+ * with a memset.  With all bits set, ops that need a lock report
+ * WS_FAIL_TIMEOUT after spin_limit attempts instead of hanging. */
+ws_status ws_debug_fill_locks(ws_table* t, int locked, ws_stream stream);
+
+/* Text of the last CUDA error seen by this library on the calling thread. */
+const char* ws_cuda_error_string(void);
+const char* ws_status_string(ws_status s);
+/* Library version, e.g. 0x000100 for 0.1.0. */
+uint32_t ws_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WARPSPEED_H */

@@ -1,0 +1,233 @@
+"""GB300-native batched concurrent hash tables (WarpSpeed, arXiv 2509.16407).
+
+Thin Python binding over the C ABI of ``include/warpspeed.h``: argument
+marshalling only; every step of an operation runs in the CUDA library.
+Batch arguments may be CUDA tensors (the fast path), CPU tensors or numpy
+arrays (the library stages them through device buffers).  Keys and values are
+64-bit (``torch.int64`` / ``torch.uint64`` / ``numpy.uint64``: the bits are
+what counts); per-op status arrays are ``uint8``.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+
+__all__ = ["Table", "WsError", "SCHEMES", "UPSERT_OPS", "MISS", "FOUND", "INSERTED", "FAIL_FULL",
+           "FAIL_BADKEY", "FAIL_TIMEOUT", "MX_QUERY", "MX_INSERT", "MX_ADD", "MX_MAX", "MX_REPLACE",
+           "MX_ERASE", "lib"]
+
+SCHEMES = {"double": 0, "p2": 1}
+UPSERT_OPS = {"add": 0, "max": 1, "replace": 2, "insert": 3}
+MISS, FOUND, INSERTED, FAIL_FULL, FAIL_BADKEY, FAIL_TIMEOUT = range(6)
+MX_QUERY, MX_INSERT, MX_ADD, MX_MAX, MX_REPLACE, MX_ERASE = range(6)
+
+
+def lib():
+    return _lib.load()
+
+
+class WsError(RuntimeError):
+    def __init__(self, rc: int, what: str):
+        L = lib()
+        msg = L.ws_status_string(rc).decode()
+        if rc == 6:
+            msg += ": " + L.ws_cuda_error_string().decode()
+        super().__init__(f"{what}: {msg} (status {rc})")
+        self.status = rc
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise WsError(rc, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_tensor(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr(x, itemsize=None):
+    if x is None:
+        return None
+    if _is_tensor(x):
+        if not x.is_contiguous():
+            raise ValueError("batch tensors must be contiguous")
+        if itemsize and x.element_size() != itemsize:
+            raise TypeError(f"expected {itemsize}-byte elements, got {x.dtype}")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("batch arrays must be C-contiguous")
+        if itemsize and x.itemsize != itemsize:
+            raise TypeError(f"expected {itemsize}-byte elements, got {x.dtype}")
+        return x.ctypes.data
+    raise TypeError(f"unsupported batch argument type {type(x)}")
+
+
+def _numel(x):
+    return x.numel() if _is_tensor(x) else x.size
+
+
+def _empty_like(x, n, kind):
+    """Output buffer on the same side as ``x``: kind 'u64' or 'u8'."""
+    if _is_tensor(x):
+        torch = _torch()
+        if kind == "u8":
+            dt = torch.uint8
+        else:
+            dt = x.dtype if x.element_size() == 8 else torch.int64
+        return torch.empty(n, dtype=dt, device=x.device, pin_memory=(not x.is_cuda and x.is_pinned()))
+    return np.empty(n, dtype=np.uint8 if kind == "u8" else np.uint64)
+
+
+class Table:
+    """A device-resident hash table (one GPU).
+
+    scheme: "double" (DoubleHT) or "p2" (P2HT); metadata: 16-bit fingerprints.
+    bucket_slots / tile / max_probe / spin_limit: 0 selects the paper's default.
+    """
+
+    def __init__(self, capacity: int, scheme: str = "double", metadata: bool = False, bucket_slots: int = 0,
+                 tile: int = 0, max_probe: int = 0, spin_limit: int = 0, device: int = -1):
+        L = lib()
+        cfg = _lib.WsConfig(int(capacity), SCHEMES[scheme], int(bool(metadata)), int(bucket_slots), int(tile),
+                            int(max_probe), int(spin_limit), int(device), 0)
+        h = ctypes.c_void_p()
+        _check(L.ws_table_create_ex(ctypes.byref(cfg), ctypes.byref(h)), "ws_table_create_ex")
+        self._h = h
+        self.scheme, self.metadata = scheme, bool(metadata)
+        self.device = self.info()["device"]
+
+    # -- lifetime / introspection -------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = _lib.WsInfo()
+        _check(lib().ws_table_info_get(self._h, ctypes.byref(inf)), "ws_table_info_get")
+        return {n: int(getattr(inf, n)) for n, _ in inf._fields_}
+
+    def _stream(self, stream):
+        if stream is None:
+            torch = _torch()
+            if torch.cuda.is_available():
+                return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+            return None
+        if hasattr(stream, "cuda_stream"):
+            return ctypes.c_void_p(stream.cuda_stream)
+        return ctypes.c_void_p(int(stream))
+
+    def set_tile(self, tile: int):
+        _check(lib().ws_set_tile(self._h, int(tile)), "ws_set_tile")
+
+    def set_spin_limit(self, spins: int):
+        _check(lib().ws_set_spin_limit(self._h, int(spins)), "ws_set_spin_limit")
+
+    def clear(self, stream=None):
+        _check(lib().ws_clear(self._h, self._stream(stream)), "ws_clear")
+
+    def count(self) -> int:
+        v = ctypes.c_uint64()
+        _check(lib().ws_count(self._h, ctypes.byref(v)), "ws_count")
+        return int(v.value)
+
+    def last_error(self) -> dict:
+        f, t, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        rc = lib().ws_last_error(self._h, ctypes.byref(f), ctypes.byref(t), ctypes.byref(b))
+        if rc == 6:
+            raise WsError(rc, "ws_last_error")
+        return {"status": rc, "full": int(f.value), "timeout": int(t.value), "badkey": int(b.value)}
+
+    def num_buckets(self) -> int:
+        v = ctypes.c_uint64()
+        _check(lib().ws_num_buckets(self._h, ctypes.byref(v)), "ws_num_buckets")
+        return int(v.value)
+
+    # -- batch operations ------------------------------------------------------------
+    def insert(self, keys, vals, return_status=False, stream=None):
+        n = _numel(keys)
+        stt = _empty_like(keys, n, "u8") if return_status else None
+        _check(lib().ws_insert_ex(self._h, _ptr(keys, 8), _ptr(vals, 8), n, _ptr(stt), self._stream(stream)),
+               "ws_insert_ex")
+        return stt
+
+    def upsert(self, keys, vals, op="add", return_status=False, stream=None):
+        n = _numel(keys)
+        stt = _empty_like(keys, n, "u8") if return_status else None
+        code = UPSERT_OPS[op] if isinstance(op, str) else int(op)
+        _check(lib().ws_upsert_ex(self._h, _ptr(keys, 8), _ptr(vals, 8), n, code, _ptr(stt),
+                                  self._stream(stream)), "ws_upsert_ex")
+        return stt
+
+    def query(self, keys, return_status=False, out=None, stream=None):
+        n = _numel(keys)
+        vals = out if out is not None else _empty_like(keys, n, "u64")
+        stt = _empty_like(keys, n, "u8") if return_status else None
+        _check(lib().ws_query_ex(self._h, _ptr(keys, 8), _ptr(vals, 8), _ptr(stt), n, self._stream(stream)),
+               "ws_query_ex")
+        return (vals, stt) if return_status else vals
+
+    def erase(self, keys, return_values=False, return_status=False, stream=None):
+        n = _numel(keys)
+        vals = _empty_like(keys, n, "u64") if return_values else None
+        stt = _empty_like(keys, n, "u8") if return_status else None
+        _check(lib().ws_erase_ex(self._h, _ptr(keys, 8), _ptr(vals, 8), _ptr(stt), n, self._stream(stream)),
+               "ws_erase_ex")
+        return vals, stt
+
+    def mixed(self, ops, keys, vals=None, return_values=True, return_status=True, stream=None):
+        n = _numel(keys)
+        vo = _empty_like(keys, n, "u64") if return_values else None
+        stt = _empty_like(keys, n, "u8") if return_status else None
+        _check(lib().ws_mixed(self._h, _ptr(ops, 1), _ptr(keys, 8), _ptr(vals, 8), _ptr(vo, 8), _ptr(stt), n,
+                              self._stream(stream)), "ws_mixed")
+        return vo, stt
+
+    def probe_cost(self, keys, stream=None):
+        """Per-key (cache lines, DRAM sectors) a query touches now (no change)."""
+        n = _numel(keys)
+        out = _empty_like(keys, n, "u64")
+        stt = _empty_like(keys, n, "u8")
+        _check(lib().ws_probe_cost(self._h, _ptr(keys, 8), _ptr(out, 8), _ptr(stt), n, self._stream(stream)),
+               "ws_probe_cost")
+        return out, stt
+
+    # -- hooks ------------------------------------------------------------------------
+    def primary_bucket(self, keys, stream=None):
+        n = _numel(keys)
+        out = _empty_like(keys, n, "u64")
+        _check(lib().ws_primary_bucket(self._h, _ptr(keys, 8), _ptr(out, 8), n, self._stream(stream)),
+               "ws_primary_bucket")
+        return out
+
+    def dump(self):
+        """(slots u64[S, 2] as (key, value), tags u16[S] or None) on the host."""
+        inf = self.info()
+        S = inf["slots"]
+        slots = np.empty((S, 2), dtype=np.uint64)
+        tags = np.empty(S, dtype=np.uint16) if inf["metadata"] else None
+        _check(lib().ws_dump(self._h, slots.ctypes.data, None if tags is None else tags.ctypes.data), "ws_dump")
+        return slots, tags
+
+    def debug_fill_locks(self, locked: bool, stream=None):
+        _check(lib().ws_debug_fill_locks(self._h, int(bool(locked)), self._stream(stream)),
+               "ws_debug_fill_locks")

@@ -1,0 +1,80 @@
+"""ctypes declarations of the C ABI in include/warpspeed.h (no logic here).
+
+The shared library is built in-tree by ``paper_2509_16407_gb300.build``.
+Loading fails loudly when it is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwarpspeed.so")
+
+vp, u64, u32, i32, u8p = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p
+st = ctypes.c_int  # ws_status
+
+
+class WsConfig(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_uint64), ("scheme", ctypes.c_int32), ("metadata", ctypes.c_int32),
+                ("bucket_slots", ctypes.c_int32), ("tile", ctypes.c_int32), ("max_probe", ctypes.c_uint32),
+                ("spin_limit", ctypes.c_uint32), ("device", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class WsInfo(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_uint64), ("buckets", ctypes.c_uint64), ("bucket_slots", ctypes.c_uint64),
+                ("tile", ctypes.c_uint64), ("max_probe", ctypes.c_uint64), ("seed1", ctypes.c_uint64),
+                ("seed2", ctypes.c_uint64), ("bytes", ctypes.c_uint64), ("scheme", ctypes.c_int32),
+                ("metadata", ctypes.c_int32), ("device", ctypes.c_int32), ("never_erased", ctypes.c_int32)]
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "ws_table_create": (st, [u64, i32, i32, ctypes.POINTER(vp)]),
+    "ws_table_create_ex": (st, [ctypes.POINTER(WsConfig), ctypes.POINTER(vp)]),
+    "ws_destroy": (st, [vp]),
+    "ws_table_info_get": (st, [vp, ctypes.POINTER(WsInfo)]),
+    "ws_clear": (st, [vp, vp]),
+    "ws_set_tile": (st, [vp, i32]),
+    "ws_set_spin_limit": (st, [vp, u32]),
+    "ws_insert": (st, [vp, vp, vp, u64, vp]),
+    "ws_insert_ex": (st, [vp, vp, vp, u64, vp, vp]),
+    "ws_upsert": (st, [vp, vp, vp, u64, i32, vp]),
+    "ws_upsert_ex": (st, [vp, vp, vp, u64, i32, vp, vp]),
+    "ws_query": (st, [vp, vp, vp, u64, vp]),
+    "ws_query_ex": (st, [vp, vp, vp, vp, u64, vp]),
+    "ws_erase": (st, [vp, vp, vp, u64, vp]),
+    "ws_erase_ex": (st, [vp, vp, vp, vp, u64, vp]),
+    "ws_mixed": (st, [vp, vp, vp, vp, vp, vp, u64, vp]),
+    "ws_probe_cost": (st, [vp, vp, vp, vp, u64, vp]),
+    "ws_count": (st, [vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "ws_last_error": (st, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                           ctypes.POINTER(ctypes.c_uint64)]),
+    "ws_num_buckets": (st, [vp, ctypes.POINTER(ctypes.c_uint64)]),
+    "ws_primary_bucket": (st, [vp, vp, vp, u64, vp]),
+    "ws_dump": (st, [vp, vp, vp]),
+    "ws_debug_fill_locks": (st, [vp, i32, vp]),
+    "ws_cuda_error_string": (ctypes.c_char_p, []),
+    "ws_status_string": (ctypes.c_char_p, [i32]),
+    "ws_version": (u32, []),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libwarpspeed.so and declare every entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(
+            f"{path} is missing: build the CUDA library first "
+            "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
