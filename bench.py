@@ -131,6 +131,24 @@ def gen_dev(seed, n, start, dev, chunk=1 << 24):
     return out
 
 
+def aggregate(ms, ops_per_rank, world, device=None):
+    """Whole-job throughput under the multi-rank contract: every rank's time is
+    reduced with MAX over ranks, ops are summed over ranks (weak scaling, each
+    rank owns its own tables).  Returns (max_ms, Gops/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms), float(ops_per_rank)], dtype=torch.float64, device=device)
+        mx = t[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        tot = t[1:].clone()
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        ms, ops = float(mx.item()), float(tot.item())
+    else:
+        ops = float(ops_per_rank)
+    return ms, ops / (ms * 1e-3) / 1e9
+
+
 def peak_gbs():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -274,13 +292,7 @@ def bench_ours(args, rank, world):
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    ms = t0.elapsed_time(t1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    total_ops = ops_per_step * args.steps * world
-    value = total_ops / (ms * 1e-3) / 1e9
+    ms, value = aggregate(t0.elapsed_time(t1), ops_per_step * args.steps, world, dev)
 
     # per-phase times, achieved bandwidth and probe costs
     peak, peak_kind = peak_gbs()
@@ -336,7 +348,7 @@ def bench_ours(args, rank, world):
                         f" 2^{int(np.log2(nq))} positive + negative queries, 2^{int(np.log2(nq))} upsert-add,"
                         f" slice erase, count), designs {[d[2] for d in designs]}",
             "slots": S, "load": args.load, "base_keys": base_n, "slice_keys": slice_n, "queries": nq,
-            "ops_per_step": ops_per_step * world,
+            "ops_per_step": ops_per_step * world, "ops_per_step_per_gpu": ops_per_step,
             "tiles": {d[2]: t.info()["tile"] for d, (_, t) in zip(designs, tables)},
             "bucket_slots": {d[2]: t.info()["bucket_slots"] for d, (_, t) in zip(designs, tables)},
             "l2": "inputs larger than L2, no flush: each table (4-4.5 GiB, 33x the 129 MB L2) is probed at"
@@ -378,16 +390,12 @@ def bench_e2e(args, tables, keys_slice, vals_slice, keys_pos, keys_neg, keys_up,
         step()
     b.record(stream)
     torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms, e2e_value = aggregate(a.elapsed_time(b), ops_per_step * args.steps, world, dev)
     n_t = len(tables)
     h2d = n_t * (keys_slice.numel() * 16 + keys_pos.numel() * 8 + keys_neg.numel() * 8 + keys_up.numel() * 16
                  + keys_slice.numel() * 8)
     d2h = n_t * (keys_pos.numel() * 8 + keys_neg.numel() * 8)
-    return {"value": round(ops_per_step * args.steps * world / (ms * 1e-3) / 1e9, 4), "unit": UNIT,
+    return {"value": round(e2e_value, 4), "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
 

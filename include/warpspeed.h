@@ -99,7 +99,8 @@ typedef struct {
   int32_t bucket_slots;  /* 0 = default */
   int32_t tile;          /* 0 = default */
   uint32_t max_probe;    /* 0 = default (80) */
-  uint32_t spin_limit;   /* lock acquisition attempts before WS_FAIL_TIMEOUT; 0 = default */
+  uint32_t spin_limit;   /* lock attempts before WS_FAIL_TIMEOUT; 0 = default (65536, each a
+                            lock-free re-probe plus <= 1 us back-off) */
   int32_t device;        /* -1 = current device */
   int32_t reserved;
 } ws_config;
@@ -127,6 +128,14 @@ ws_status ws_clear(ws_table* t, ws_stream stream);
 /* Change the tile size used by later calls (4, 8, 16 or 32). */
 ws_status ws_set_tile(ws_table* t, int tile);
 ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
+
+/* Tuning options (affect speed only, never results).
+ *  WS_OPT_PREFETCH: L2 prefetch of each op's first bucket(s) (double hashing: b_0;
+ *  two-choice: b_0 and b_1; metadata: their tag lines) by one lane per op before the
+ *  tiles probe.  Bits 0-1: 0 off, 1 per-line prefetch, 2 bulk-range prefetch; bit 2:
+ *  issue the prefetches one warp chunk ahead. */
+enum { WS_OPT_PREFETCH = 1 };
+ws_status ws_set_option(ws_table* t, int option, int64_t value);
 
 /* Insert-if-unique (§5.1 Upsert with the empty callback).  status_out: per-op
  * WS_INSERTED / WS_FOUND (already present, value kept) / WS_FAIL_*; nullable. */

@@ -37,6 +37,7 @@ SIGNATURES = {
     "ws_clear": (st, [vp, vp]),
     "ws_set_tile": (st, [vp, i32]),
     "ws_set_spin_limit": (st, [vp, u32]),
+    "ws_set_option": (st, [vp, i32, ctypes.c_int64]),
     "ws_insert": (st, [vp, vp, vp, u64, vp]),
     "ws_insert_ex": (st, [vp, vp, vp, u64, vp, vp]),
     "ws_upsert": (st, [vp, vp, vp, u64, i32, vp]),

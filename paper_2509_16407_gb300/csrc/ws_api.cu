@@ -31,8 +31,9 @@ void note_cuda(cudaError_t e, const char* where) {
 constexpr u64 kSeed1 = 0x243f6a8885a308d3ull;  // hex digits of pi: fixed, documented seeds
 constexpr u64 kSeed2 = 0x13198a2e03707344ull;
 constexpr uint32_t kDefaultProbe = 80;
-constexpr uint32_t kDefaultSpin = 1u << 20;
-constexpr u64 kStageOps = 1ull << 22;  // ops per staging chunk (host-buffer path)
+constexpr uint32_t kDefaultSpin = 1u << 16;  // attempts; each costs a probe + <= 1 us back-off
+constexpr u64 kStageOps = 1ull << 22;
+constexpr int kDefaultPrefetch = 0;  // L2 prefetch mode (see WS_OPT_PREFETCH)  // ops per staging chunk (host-buffer path)
 
 struct DeviceGuard {
   int prev = -1;
@@ -327,6 +328,7 @@ ws_status ws_table_create_ex(const ws_config* cfg, ws_table** out) {
   tv.pmax = t->pmax;
   tv.spin_limit = t->spin;
   tv.shortcut = 1;
+  tv.prefetch = kDefaultPrefetch;
   cudaError_t e = cudaMemset(tv.slots, 0, t->S * sizeof(ws::Slot));
   if (e == cudaSuccess && meta) e = cudaMemset(tv.tags, 0, t->S * 2);
   if (e == cudaSuccess) e = cudaMemset(tv.locks, 0, lock_words * 4);
@@ -398,6 +400,17 @@ ws_status ws_set_tile(ws_table* t, int tile) {
   if (!t || (tile != 4 && tile != 8 && tile != 16 && tile != 32)) return WS_ERR_INVALID;
   t->T = tile;
   return WS_OK;
+}
+
+ws_status ws_set_option(ws_table* t, int option, int64_t value) {
+  if (!t) return WS_ERR_INVALID;
+  switch (option) {
+    case WS_OPT_PREFETCH:
+      if (value < 0 || value > 6 || (value & 3) == 3) return WS_ERR_INVALID;
+      t->tv.prefetch = (int)value;
+      return WS_OK;
+  }
+  return WS_ERR_INVALID;
 }
 
 ws_status ws_set_spin_limit(ws_table* t, uint32_t spins) {

@@ -57,6 +57,7 @@ struct TableView {
   u32 pmax;       // double hashing: buckets a probe sequence may visit (<= nb)
   u32 spin_limit; // lock attempts before giving up
   int shortcut;   // P2: no erase ever ran, so the primary-fill shortcut is exact
+  int prefetch;   // L2 prefetch of first buckets: bits 0-1 method (0 off, 1 line, 2 bulk), bit 2 lead one chunk
 };
 
 struct BatchArgs {
@@ -117,14 +118,16 @@ __device__ __forceinline__ void st_slot_release(Slot* p, u64 k, u64 v) {
       : "memory");
 }
 
-// 128-bit compare-and-swap of a whole slot; returns true on success.
+// 128-bit compare-and-swap of a whole slot (relaxed: the pair itself is the
+// published datum; a lock release or a release store orders it where needed).
+// Returns true on success.
 __device__ __forceinline__ bool cas_slot(Slot* p, u64 ek, u64 ev, u64 nk, u64 nv) {
   u64 ok, ov;
   asm volatile(
       "{\n\t.reg .b128 d, c, s;\n\t"
       "mov.b128 c, {%2, %3};\n\t"
       "mov.b128 s, {%4, %5};\n\t"
-      "atom.acq_rel.gpu.global.cas.b128 d, [%6], c, s;\n\t"
+      "atom.relaxed.gpu.global.cas.b128 d, [%6], c, s;\n\t"
       "mov.b128 {%0, %1}, d;\n\t}"
       : "=l"(ok), "=l"(ov)
       : "l"(ek), "l"(ev), "l"(nk), "l"(nv), "l"(p)
@@ -132,9 +135,11 @@ __device__ __forceinline__ bool cas_slot(Slot* p, u64 ek, u64 ev, u64 nk, u64 nv
   return ok == ek && ov == ev;
 }
 
+// Tag claim (acquire: the claimer's later pair store must come after the
+// eraser's tombstone of that slot, which the eraser released with the tag).
 __device__ __forceinline__ u16 cas_tag(u16* p, u16 expect, u16 desired) {
   u16 old;
-  asm volatile("atom.acq_rel.gpu.global.cas.b16 %0, [%1], %2, %3;"
+  asm volatile("atom.acquire.gpu.global.cas.b16 %0, [%1], %2, %3;"
                : "=h"(old)
                : "l"(p), "h"(expect), "h"(desired)
                : "memory");
@@ -171,6 +176,15 @@ __device__ __forceinline__ void red_max_u64(u64* p, u64 v) {
 
 __device__ __forceinline__ void st_u64_relaxed(u64* p, u64 v) {
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// L2 prefetch of one 128-byte line, and of a 16-byte-multiple range through
+// the bulk-copy unit.
+__device__ __forceinline__ void prefetch_line_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void prefetch_bulk_l2(const void* p, u32 bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // Tag loads of 16, 8, 4 or 2 bytes (one lane's share of a 64-byte tag line).

@@ -34,7 +34,9 @@
 //     CAS (then the tag becomes TOMB).  A tombstone never turns back into
 //     EMPTY, which keeps every early-exit rule valid.
 // Every lock wait is bounded: after spin_limit attempts the op reports
-// WS_FAIL_TIMEOUT instead of spinning on.
+// WS_FAIL_TIMEOUT instead of spinning on.  A tile waiting for a lock keeps
+// re-probing lock-free and finishes without the lock as soon as the key
+// appears (a concurrent inserter of the same key got there first).
 #pragma once
 #include "ws_device.cuh"
 
@@ -76,6 +78,7 @@ struct TileOps {
     u64 idx, val;     // where the key is (found)
     bool has_free;
     u64 fidx, fk, fv; // free slot to claim and its observed content (tag in fk for META)
+    bool stuck;       // a wait for a claimed slot's pair ran out
   };
 
   __device__ static __forceinline__ u32 nprobe(const TableView& tv) {
@@ -90,6 +93,34 @@ struct TileOps {
     u64 b1 = h2 & tv.nb_mask;
     if (b1 == b0) b1 = (b0 + 1) & tv.nb_mask;
     return b1;
+  }
+
+  // Bring the first bucket(s) of key K into L2 ahead of the tile that will
+  // probe them (one lane per op, so a warp has 32 ops' lines in flight while
+  // its tiles work through the ops one at a time).  Double hashing: b_0;
+  // two-choice: b_0 and b_1.  Metadata tables: the 64-byte tag lines.
+  __device__ static __forceinline__ void prefetch_one(const TableView& tv, u64 b, int method) {
+    if (META) {
+      const u16* tp = tv.tags + b * 32;
+      if (method == 2)
+        ptx::prefetch_bulk_l2(tp, 64);
+      else
+        ptx::prefetch_line_l2(tp);
+    } else {
+      const Slot* sp = tv.slots + b * B;
+      if (method == 2) {
+        ptx::prefetch_bulk_l2(sp, B * 16);
+      } else {
+#pragma unroll
+        for (int l = 0; l < (B * 16) / 128; ++l) ptx::prefetch_line_l2(sp + l * 8);
+      }
+    }
+  }
+  __device__ static __forceinline__ void prefetch_key(const TableView& tv, u64 K, int method) {
+    if (is_sentinel(K)) return;
+    const u64 h1 = fmix64(K ^ tv.seed1);
+    prefetch_one(tv, h1 & tv.nb_mask, method);
+    if (SCHEME == SCHEME_P2 && tv.nb_mask) prefetch_one(tv, bucket(tv, h1, fmix64(K ^ tv.seed2), 1), method);
   }
 
   // ----------------------------------------------------------------------
@@ -143,6 +174,7 @@ struct TileOps {
 
   __device__ static Scan scan_plain(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2) {
     Scan r;
+    r.stuck = false;
     r.found = false;
     r.has_free = false;
     r.idx = r.val = r.fidx = r.fk = r.fv = 0;
@@ -309,14 +341,33 @@ struct TileOps {
   }
 
   // Reads the candidate slots of a tag match mask; true if one holds K.
-  __device__ static __forceinline__ bool verify(const TableView& tv, u64 b, unsigned mm, u64 K,
-                                                u64& idx, u64& val) {
+  // With WAIT (lock-free inserts, where no erase runs concurrently) a slot
+  // whose tag is claimed but whose pair is not stored yet (key EMPTY/TOMB) is
+  // re-read until the claimer's release store lands, so a same-key inserter
+  // cannot miss a copy being written.  *stuck reports a wait that ran out.
+  template <bool WAIT = false>
+  __device__ static __forceinline__ bool verify(const TableView& tv, const TileCtx<T>& c, u64 b, unsigned mm,
+                                                u64 K, u64& idx, u64& val, bool* stuck = nullptr) {
     while (mm) {
       const int q = __ffs(mm) - 1;
       mm &= mm - 1;
       const u64 si = b * 32 + (u64)q;
       u64 k, v;
       ptx::ld_slot(tv.slots + si, k, v);  // same address on every lane: one request
+      if (WAIT) {
+        k = c.shfl(k, 0);
+        v = c.shfl(v, 0);
+        for (u32 n = 0; k == KEY_EMPTY || k == KEY_TOMB; ++n) {
+          if (n >= tv.spin_limit) {
+            *stuck = true;
+            break;
+          }
+          __nanosleep(64);
+          ptx::ld_slot(tv.slots + si, k, v);
+          k = c.shfl(k, 0);
+          v = c.shfl(v, 0);
+        }
+      }
       if (k == K) {
         idx = si;
         val = v;
@@ -353,7 +404,7 @@ struct TileOps {
         *lines += 1 + nc;
       }
       u64 idx, val;
-      if (verify(tv, b, mm, K, idx, val)) return {true, idx, val};
+      if (verify(tv, c, b, mm, K, idx, val)) return {true, idx, val};
       if (SCHEME == SCHEME_DOUBLE) {
         if (me) break;
       } else if (i == 0 && tv.shortcut && (u32)(32 - __popc(mf)) < FILL_SHORTCUT) {
@@ -363,8 +414,10 @@ struct TileOps {
     return {false, 0, 0};
   }
 
+  template <bool WAIT = false>
   __device__ static Scan scan_meta(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2) {
     Scan r;
+    r.stuck = false;
     r.found = false;
     r.has_free = false;
     r.idx = r.val = r.fidx = r.fk = r.fv = 0;
@@ -375,7 +428,7 @@ struct TileOps {
         const u64 b = bucket(tv, h1, h2, i);
         unsigned mm, me, mf;
         tag_masks(tv, c, b, kt, mm, me, mf);
-        if (verify(tv, b, mm, K, r.idx, r.val)) {
+        if (verify<WAIT>(tv, c, b, mm, K, r.idx, r.val, &r.stuck)) {
           r.found = true;
           return r;
         }
@@ -397,7 +450,7 @@ struct TileOps {
       const u64 b = bucket(tv, h1, h2, bi);
       unsigned mm, me, mf;
       tag_masks(tv, c, b, kt, mm, me, mf);
-      if (verify(tv, b, mm, K, r.idx, r.val)) {
+      if (verify<WAIT>(tv, c, b, mm, K, r.idx, r.val, &r.stuck)) {
         r.found = true;
         return r;
       }
@@ -434,9 +487,10 @@ struct TileOps {
     if (META) return find_meta(tv, c, K, h1, h2);
     return find_plain(tv, c, K, h1, h2);
   }
+  template <bool WAIT = false>
   __device__ static __forceinline__ Scan scan(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1,
                                               u64 h2) {
-    if (META) return scan_meta(tv, c, K, h1, h2);
+    if (META) return scan_meta<WAIT>(tv, c, K, h1, h2);
     return scan_plain(tv, c, K, h1, h2);
   }
 
@@ -469,25 +523,27 @@ struct TileOps {
       ptx::st_u64_relaxed(vp, V);
   }
 
-  __device__ static bool lock(const TableView& tv, const TileCtx<T>& c, u64 b) {
-    int ok = 1;
+  // One test-and-test-and-set attempt on the lock bit of bucket b by the
+  // leader lane; the outcome is returned on every lane of the tile.
+  __device__ static __forceinline__ bool try_lock(const TableView& tv, const TileCtx<T>& c, u64 b) {
+    int ok = 0;
     if (c.tl == 0) {
       u32* w = tv.locks + (b >> 5);
       const u32 bit = 1u << (b & 31);
-      u32 tries = 0, ns = 0;
-      for (;;) {
-        if (!(ptx::ld_u32_relaxed(w) & bit) && !(ptx::atom_or_acquire(w, bit) & bit)) break;
-        if (++tries >= tv.spin_limit) {
-          ok = 0;
-          break;
-        }
-        ns = ns ? (ns < 1024u ? ns * 2u : 1024u) : 32u;
-        __nanosleep(ns);
-      }
+      ok = (!(ptx::ld_u32_relaxed(w) & bit) && !(ptx::atom_or_acquire(w, bit) & bit)) ? 1 : 0;
     }
     ok = c.shfl(ok, 0);
     __syncwarp(c.mask);
     return ok != 0;
+  }
+
+  // Back-off between lock attempts (leader sleeps, the tile waits for it).
+  __device__ static __forceinline__ void backoff(const TileCtx<T>& c, u32& ns) {
+    if (c.tl == 0) {
+      ns = ns ? (ns < 1024u ? ns * 2u : 1024u) : 32u;
+      __nanosleep(ns);
+    }
+    __syncwarp(c.mask);
   }
 
   __device__ static __forceinline__ void unlock(const TableView& tv, const TileCtx<T>& c, u64 b) {
@@ -524,17 +580,56 @@ struct TileOps {
     return h.found ? ST_FOUND : ST_MISS;
   }
 
+  // LOCKFREE: the caller guarantees that no erase runs in the same launch (a
+  // plain insert / upsert call is one phase).
+  template <bool LOCKFREE>
   __device__ static u8 do_upsert(const TableView& tv, const TileCtx<T>& c, u64 K, u64 V, int op,
                                  int& dcount) {
     if (is_sentinel(K)) return ST_BADKEY;
     const u64 h1 = fmix64(K ^ tv.seed1), h2 = fmix64(K ^ tv.seed2);
+    if (LOCKFREE && SCHEME == SCHEME_DOUBLE) {
+      // Without erases, free slots only disappear, so every inserter of K
+      // targets the first free slot of K's probe sequence: the CAS winner
+      // places K and a loser's rescan finds it (with metadata, verify waits
+      // out a claimed-but-unwritten slot).  No lock is needed; the lock of
+      // §4.1 is for inserts racing erases (mixed batches) and for two-choice
+      // placement, whose choice depends on the moment's bucket loads.
+      for (int attempt = 0; attempt < 256; ++attempt) {
+        const Scan r = scan<true>(tv, c, K, h1, h2);
+        if (r.stuck) return ST_TIMEOUT;
+        if (r.found) {
+          if (c.tl == 0) apply(tv, r.idx, op, V);
+          return ST_FOUND;
+        }
+        if (!r.has_free) return ST_FULL;
+        if (claim(tv, c, r, K, V)) {
+          ++dcount;
+          return ST_INSERTED;
+        }
+      }
+      return ST_TIMEOUT;
+    }
     const Hit h = find(tv, c, K, h1, h2);
     if (h.found) {
       if (c.tl == 0) apply(tv, h.idx, op, V);
       return ST_FOUND;
     }
+    // Absent: take the primary bucket's lock so that inserters of this key
+    // agree on one slot (§4.1).  While another tile holds it -- often one
+    // inserting this very key -- probe again lock-free: once the key is
+    // present its slot never moves, so the update needs no lock.  This keeps
+    // a batch's many copies of a hot key from queueing on one lock bit.
     const u64 b0 = bucket(tv, h1, h2, 0);
-    if (!lock(tv, c, b0)) return ST_TIMEOUT;
+    for (u32 tries = 0, ns = 0;;) {
+      if (try_lock(tv, c, b0)) break;
+      const Hit again = find(tv, c, K, h1, h2);
+      if (again.found) {
+        if (c.tl == 0) apply(tv, again.idx, op, V);
+        return ST_FOUND;
+      }
+      if (++tries >= tv.spin_limit) return ST_TIMEOUT;
+      backoff(c, ns);
+    }
     u8 st = ST_TIMEOUT;
     for (int attempt = 0; attempt < 256; ++attempt) {
       const Scan r = scan(tv, c, K, h1, h2);
@@ -613,13 +708,29 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
   int dcount = 0;
   const u64 nchunks = (a.n + 31) / 32;
   const u64 stride = (u64)gridDim.x * kWarps;
-  for (u64 ch = (u64)blockIdx.x * kWarps + w; ch < nchunks; ch += stride) {
+  const int pf_method = (KIND == KIND_PROBE) ? 0 : (tv.prefetch & 3);
+  const bool pf_lead = (tv.prefetch & 4) != 0;
+  u64 ch = (u64)blockIdx.x * kWarps + w;
+  // keys of the chunk about to be staged (prefetched one chunk ahead with pf_lead)
+  u64 next_key = 0;
+  if (ch < nchunks) {
+    const u64 gi0 = ch * 32 + lane;
+    next_key = gi0 < a.n ? a.keys[gi0] : 0;
+    if (pf_method && gi0 < a.n) Ops::prefetch_key(tv, next_key, pf_method);
+  }
+  for (; ch < nchunks; ch += stride) {
     const u64 base = ch * 32;
     const u64 gi = base + lane;
     const bool inb = gi < a.n;
-    s_key[w][lane] = inb ? a.keys[gi] : 0;
+    s_key[w][lane] = next_key;
     if (KIND == KIND_UPSERT || KIND == KIND_MIXED) s_val[w][lane] = (inb && a.vals) ? a.vals[gi] : 0;
     if (KIND == KIND_MIXED) s_op[w][lane] = inb ? a.ops[gi] : 0;
+    {
+      const u64 nch = ch + stride;
+      const u64 ngi = nch * 32 + lane;
+      next_key = (nch < nchunks && ngi < a.n) ? a.keys[ngi] : 0;
+      if (pf_method && pf_lead && nch < nchunks && ngi < a.n) Ops::prefetch_key(tv, next_key, pf_method);
+    }
     __syncwarp();
     const int cnt = (a.n - base) < 32 ? (int)(a.n - base) : 32;
     for (int jj = 0; jj < T; ++jj) {
@@ -633,17 +744,17 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
       } else if (KIND == KIND_PROBE) {
         st = Ops::do_probe(tv, c, K, out);
       } else if (KIND == KIND_UPSERT) {
-        st = Ops::do_upsert(tv, c, K, s_val[w][j], a.op, dcount);
+        st = Ops::template do_upsert<true>(tv, c, K, s_val[w][j], a.op, dcount);
       } else if (KIND == KIND_ERASE) {
         st = Ops::do_erase(tv, c, K, out, dcount);
       } else {
         const u8 code = s_op[w][j];
         switch (code) {
           case MX_QUERY: st = Ops::do_query(tv, c, K, out); break;
-          case MX_INSERT: st = Ops::do_upsert(tv, c, K, s_val[w][j], OP_INSERT, dcount); break;
-          case MX_ADD: st = Ops::do_upsert(tv, c, K, s_val[w][j], OP_ADD, dcount); break;
-          case MX_MAX: st = Ops::do_upsert(tv, c, K, s_val[w][j], OP_MAX, dcount); break;
-          case MX_REPLACE: st = Ops::do_upsert(tv, c, K, s_val[w][j], OP_REPLACE, dcount); break;
+          case MX_INSERT: st = Ops::template do_upsert<false>(tv, c, K, s_val[w][j], OP_INSERT, dcount); break;
+          case MX_ADD: st = Ops::template do_upsert<false>(tv, c, K, s_val[w][j], OP_ADD, dcount); break;
+          case MX_MAX: st = Ops::template do_upsert<false>(tv, c, K, s_val[w][j], OP_MAX, dcount); break;
+          case MX_REPLACE: st = Ops::template do_upsert<false>(tv, c, K, s_val[w][j], OP_REPLACE, dcount); break;
           case MX_ERASE: st = Ops::do_erase(tv, c, K, out, dcount); break;
           default: st = ST_BADKEY; break;
         }

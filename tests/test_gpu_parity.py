@@ -335,24 +335,33 @@ def test_full_reports_validated(ws, oracle_mod, scheme, meta):
 
 @pytest.mark.parametrize("scheme,meta", DESIGNS, ids=DESIGN_IDS)
 def test_lock_timeout_is_bounded(ws, oracle_mod, scheme, meta):
+    """Every lock bit set from the host: absent-key inserts that need the lock
+    (mixed batches; two-choice plain inserts) report TIMEOUT after spin_limit
+    attempts instead of hanging; lock-free paths are unaffected."""
     t = ws.Table(1 << 12, scheme, meta, spin_limit=64)
-    keys = W.distinct_keys(8, 1000)
+    keys = W.distinct_keys(8, 1500)
     t.insert(dev(keys[:500]), dev(keys[:500]))
     t.debug_fill_locks(True)
-    st = host(t.insert(dev(keys[500:]), dev(keys[500:]), return_status=True))
-    assert (st == ws.FAIL_TIMEOUT).all()
+    ops = np.full(500, W.MX_INSERT, np.uint8)
+    _, st = t.mixed(dev(ops), dev(keys[500:1000]), dev(keys[500:1000]))
+    assert (host(st) == ws.FAIL_TIMEOUT).all()
     # present keys need no lock (in-place update), queries are lock-free
     st = host(t.upsert(dev(keys[:500]), dev(np.ones(500, np.uint64)), op="add", return_status=True))
     assert (st == ws.FOUND).all()
-    v, s = t.query(dev(keys), return_status=True)
+    v, s = t.query(dev(keys[:1000]), return_status=True)
     assert (host(s)[:500] == ws.FOUND).all() and (host(s)[500:] == ws.MISS).all()
     assert (host(v)[:500] == keys[:500] + np.uint64(1)).all()
+    # plain inserts: two-choice placement needs the lock, double hashing does not
+    st = host(t.insert(dev(keys[1000:]), dev(keys[1000:]), return_status=True))
+    want = ws.INSERTED if scheme == "double" else ws.FAIL_TIMEOUT
+    assert (st == want).all()
     e = t.last_error()
-    assert e["status"] == 5 and e["timeout"] == 500
+    assert e["status"] == 5 and e["timeout"] == 500 + (0 if scheme == "double" else 500)
     t.debug_fill_locks(False)
-    assert (host(t.insert(dev(keys[500:]), dev(keys[500:]), return_status=True)) == ws.INSERTED).all()
-    assert t.count() == 1000
-    check_layout(oracle_mod, t, 1000)
+    rest = keys[500:] if scheme == "p2" else keys[500:1000]
+    assert (host(t.insert(dev(rest), dev(rest), return_status=True)) == ws.INSERTED).all()
+    assert t.count() == 1500
+    check_layout(oracle_mod, t, 1500)
 
 
 def test_sentinel_keys_and_bad_codes(ws):
