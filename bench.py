@@ -53,6 +53,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--sweep", default="", help="write the load/tile sweep as JSON lines to this file")
     p.add_argument("--sweep-log2-slots", default="28,22")
+    p.add_argument("--workload", default="config2", choices=["config2", "batched", "serve"],
+                   help="config2 = the default line; batched = 1024 uneven tables in one graph launch")
+    p.add_argument("--tables", type=int, default=1024)
     return p.parse_args()
 
 
@@ -463,6 +466,125 @@ def bench_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# batched mode (config 4): 1024 tables, capacities log-uniform 2^10..2^22,
+# ops log-uniform 2^8..2^20 (inserts = min(n/2, 0.85 cap), the rest queries,
+# half present / half absent); one persistent graph launch per step vs one
+# insert + one query launch per table, identical results required.
+# ---------------------------------------------------------------------------
+def bench_batched(args):
+    import torch
+    import oracle
+    import paper_2509_16407_gb300 as ws
+    from paper_2509_16407_gb300 import autotune
+    dev = torch.device("cuda", 0)
+    n_t = args.tables
+    caps = W.log_uniform_int(41, n_t, 1 << 10, 1 << 22)
+    nops = W.log_uniform_int(42, n_t, 1 << 8, 1 << 20)
+    t_tune = time.time()
+    choice, timings = autotune.tune(log=lambda m: print(m, file=sys.stderr, flush=True))
+    t_tune = time.time() - t_tune
+    specs = []
+    for i in range(n_t):
+        cap, n = int(caps[i]), int(nops[i])
+        n_ins = min(n // 2, int(0.85 * cap))
+        n_q = n - n_ins
+        k = W.distinct_keys(7_000_003 + i, n_ins + n_q // 2)
+        ins, neg = k[:n_ins], k[n_ins:]
+        pos = ins[W.splitmix64(88 + i, n_q - n_q // 2) % np.uint64(n_ins)]
+        specs.append((cap, to_dev(ins, dev), to_dev(W.splitmix64(99 + i, n_ins), dev),
+                      to_dev(np.concatenate([pos, neg]), dev)))
+    total_ops = sum(int(nops[i]) for i in range(n_t))
+
+    def make(tuned):
+        tabs, outs = [], []
+        for i, (cap, ki, vi, q) in enumerate(specs):
+            if tuned:
+                sch, meta, B, T = autotune.config_for(cap, choice)
+                t = ws.Table(cap, sch, meta, bucket_slots=B, tile=T)
+            else:
+                t = ws.Table(cap, "double", False)
+            outs.append((torch.empty(ki.numel(), dtype=torch.uint8, device=dev),
+                         torch.empty(q.numel(), dtype=torch.int64, device=dev),
+                         torch.empty(q.numel(), dtype=torch.uint8, device=dev)))
+            tabs.append(t)
+        return tabs, outs
+
+    def run_plain(tabs, outs):
+        for (cap, ki, vi, q), t, (si, qv, qs) in zip(specs, tabs, outs):
+            lib = ws.lib()
+            lib.ws_insert_ex(t.handle, ki.data_ptr(), vi.data_ptr(), ki.numel(), si.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+            lib.ws_query_ex(t.handle, q.data_ptr(), qv.data_ptr(), qs.data_ptr(), q.numel(),
+                            torch.cuda.current_stream().cuda_stream)
+
+    def timed(fn, tabs, reps):
+        ts = []
+        for _ in range(reps):
+            for t in tabs:
+                t.clear()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    tuned, tout = make(True)
+    items = []
+    for (cap, ki, vi, q), t, (si, qv, qs) in zip(specs, tuned, tout):
+        items += [(t, ws.BK_INSERT, ki, vi, None, si, 0), (t, ws.BK_QUERY, q, None, qv, qs, 1)]
+    plan = ws.BatchPlan(items)
+    reps = max(args.steps, 3)
+    timed(plan.launch, tuned, args.warmup)
+    ts_batched = timed(plan.launch, tuned, reps)
+    res_b = [(si.clone(), qv.clone(), qs.clone()) for si, qv, qs in tout]
+    timed(lambda: run_plain(tuned, tout), tuned, 1)
+    ts_plain_tuned = timed(lambda: run_plain(tuned, tout), tuned, reps)
+    same = all(torch.equal(a, b) for ra, rb in zip(res_b, tout) for a, b in zip(ra, rb))
+    cfg_count = {}
+    for t in tuned:
+        inf = t.info()
+        key = f"{'P2HT' if inf['scheme'] else 'DoubleHT'}{'(M)' if inf['metadata'] else ''}/B{inf['bucket_slots']}/T{inf['tile']}"
+        cfg_count[key] = cfg_count.get(key, 0) + 1
+    fallback = plan.info()["fallback_items"]
+    plan.close()
+    for t in tuned:
+        t.close()
+    torch.cuda.empty_cache()
+    dflt, dout = make(False)
+    timed(lambda: run_plain(dflt, dout), dflt, 1)
+    ts_plain_default = timed(lambda: run_plain(dflt, dout), dflt, reps)
+    same_default = all(torch.equal(a, b) for ra, rb in zip(res_b, dout) for a, b in zip(ra, rb))
+    # oracle on a sample of tables
+    bad = 0
+    for i in range(0, n_t, max(1, n_t // 48)):
+        cap, ki, vi, q = specs[i]
+        om = oracle.OracleMap()
+        wst = om.insert(ki.cpu().numpy().view(np.uint64), vi.cpu().numpy().view(np.uint64))
+        wv, wq = om.query(q.cpu().numpy().view(np.uint64))
+        si, qv, qs = res_b[i]
+        bad += int(not ((si.cpu().numpy() == wst).all() and (qv.cpu().numpy().view(np.uint64) == wv).all()
+                        and (qs.cpu().numpy() == wq).all()))
+    med = statistics.median
+    return {
+        "metric": "batched Gops/s (1024 tables, one graph launch) vs per-table launches", "unit": UNIT,
+        "value": round(total_ops / (med(ts_batched) * 1e-3) / 1e9, 4), "higher_is_better": True,
+        "plain_tuned_gops": round(total_ops / (med(ts_plain_tuned) * 1e-3) / 1e9, 4),
+        "plain_default_gops": round(total_ops / (med(ts_plain_default) * 1e-3) / 1e9, 4),
+        "ms": {"batched": round(med(ts_batched), 3), "plain_tuned": round(med(ts_plain_tuned), 3),
+               "plain_default": round(med(ts_plain_default), 3)},
+        "identical_results": {"batched_vs_plain_tuned": same, "batched_vs_plain_default": same_default},
+        "oracle_sampled_tables_mismatching": bad, "total_ops": total_ops, "tables": n_t,
+        "launches": {"batched": 1, "plain": 2 * n_t}, "configs": cfg_count, "fallback_items": fallback,
+        "autotune_seconds": round(t_tune, 1),
+        "autotune_choice": {str(k): "/".join(map(str, v)) for k, v in choice.items()},
+        "config": {"workload": "config 4: capacities log-uniform 2^10-2^22, ops log-uniform 2^8-2^20, load 0.85",
+                   "data": "synthetic"}}
+
+
+# ---------------------------------------------------------------------------
 # load / tile sweep (config 2): one JSON line per (slots, design, tile, load)
 # ---------------------------------------------------------------------------
 def sweep(args):
@@ -539,6 +661,9 @@ def main():
         dist.init_process_group("nccl")
     if args.sweep:
         sweep(args)
+        return
+    if args.workload == "batched":
+        print(json.dumps(bench_batched(args)), flush=True)
         return
     res = bench_ours(args, rank, world)
     if rank == 0:

@@ -197,6 +197,14 @@ ws_status ws_num_buckets(const ws_table* t, uint64_t* out);
 ws_status ws_primary_bucket(ws_table* t, const uint64_t* keys, uint64_t* out, uint64_t n,
                             ws_stream stream);
 
+/* Insert every live pair of src into dst (insert-if-unique), reading src's
+ * slot array in place -- the growth step of a serving loop (allocate a larger
+ * dst, rehash, destroy src).  src must not change meanwhile (its last stream
+ * is synchronised first if it differs from stream).  status_out (nullable,
+ * device u8[src slots]) gets WS_INSERTED / WS_FOUND / WS_FAIL_* per source slot
+ * and WS_MISS for empty or erased source slots.  Asynchronous on stream. */
+ws_status ws_rehash(ws_table* src, ws_table* dst, uint8_t* status_out, ws_stream stream);
+
 /* Copy the slot array (S x {key, val}, 16 B each) and, for metadata tables,
  * the tag array (S x u16) to host memory.  Synchronising.  host_tags may be
  * NULL.  For layout checks and snapshots. */
@@ -206,6 +214,39 @@ ws_status ws_dump(ws_table* t, void* host_slots, void* host_tags);
  * with a memset.  With all bits set, ops that need a lock report
  * WS_FAIL_TIMEOUT after spin_limit attempts instead of hanging. */
 ws_status ws_debug_fill_locks(ws_table* t, int locked, ws_stream stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched mode: many tables and their op batches in one persistent kernel per
+ * phase, captured once into a CUDA graph (a plan) and replayed with one launch.
+ * Items of one phase run concurrently (the per-table phase contract holds per
+ * phase); phases run in increasing order.  Every pointer must be a device
+ * pointer on the tables' device (all tables on one device) and stay valid
+ * while the plan exists; the plan copies the item list, so item arrays may be
+ * rewritten in place between launches.  Tables whose (scheme, metadata, bucket,
+ * tile) configuration is outside the compiled menu run as separate kernels in
+ * the same graph (ws_batch_plan_info reports how many).  The plan owns its
+ * descriptor, chunk and ticket arrays (allocated at create). */
+typedef enum { WS_BK_INSERT = 0, WS_BK_UPSERT = 1, WS_BK_QUERY = 2, WS_BK_ERASE = 3 } ws_batch_kind;
+typedef struct {
+  ws_table* table;
+  int32_t kind;   /* ws_batch_kind */
+  int32_t op;     /* ws_upsert_op, for WS_BK_UPSERT */
+  int32_t phase;  /* >= 0 */
+  int32_t reserved;
+  const uint64_t* keys;
+  const uint64_t* vals;  /* insert / upsert */
+  uint64_t* vals_out;    /* query / erase (nullable for erase) */
+  uint8_t* status_out;   /* nullable */
+  uint64_t n;
+} ws_batch_item;
+typedef struct ws_batch_plan ws_batch_plan;
+ws_status ws_batch_plan_create(const ws_batch_item* items, uint64_t n_items, ws_batch_plan** out);
+/* One graph launch on stream; asynchronous. */
+ws_status ws_batch_plan_launch(ws_batch_plan* plan, ws_stream stream);
+ws_status ws_batch_plan_info(const ws_batch_plan* plan, uint64_t* n_phases, uint64_t* n_chunks,
+                             uint64_t* n_fallback_items);
+/* Waits for the device, then frees the plan's device memory. */
+ws_status ws_batch_plan_destroy(ws_batch_plan* plan);
 
 /* Text of the last CUDA error seen by this library on the calling thread. */
 const char* ws_cuda_error_string(void);

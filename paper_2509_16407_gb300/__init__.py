@@ -17,12 +17,13 @@ from . import _lib
 
 __all__ = ["Table", "WsError", "SCHEMES", "UPSERT_OPS", "MISS", "FOUND", "INSERTED", "FAIL_FULL",
            "FAIL_BADKEY", "FAIL_TIMEOUT", "MX_QUERY", "MX_INSERT", "MX_ADD", "MX_MAX", "MX_REPLACE",
-           "MX_ERASE", "lib"]
+           "MX_ERASE", "lib", "BatchPlan", "BK_INSERT", "BK_UPSERT", "BK_QUERY", "BK_ERASE"]
 
 SCHEMES = {"double": 0, "p2": 1}
 UPSERT_OPS = {"add": 0, "max": 1, "replace": 2, "insert": 3}
 MISS, FOUND, INSERTED, FAIL_FULL, FAIL_BADKEY, FAIL_TIMEOUT = range(6)
 MX_QUERY, MX_INSERT, MX_ADD, MX_MAX, MX_REPLACE, MX_ERASE = range(6)
+BK_INSERT, BK_UPSERT, BK_QUERY, BK_ERASE = range(4)
 
 
 def lib():
@@ -223,6 +224,15 @@ class Table:
                "ws_primary_bucket")
         return out
 
+    def rehash_into(self, dst: "Table", return_status=False, stream=None):
+        """Insert every live pair of this table into ``dst`` (growth step)."""
+        stt = None
+        if return_status:
+            torch = _torch()
+            stt = torch.empty(self.info()["slots"], dtype=torch.uint8, device=f"cuda:{self.device}")
+        _check(lib().ws_rehash(self._h, dst._h, _ptr(stt), self._stream(stream)), "ws_rehash")
+        return stt
+
     def dump(self):
         """(slots u64[S, 2] as (key, value), tags u16[S] or None) on the host."""
         inf = self.info()
@@ -235,3 +245,47 @@ class Table:
     def debug_fill_locks(self, locked: bool, stream=None):
         _check(lib().ws_debug_fill_locks(self._h, int(bool(locked)), self._stream(stream)),
                "ws_debug_fill_locks")
+
+
+class BatchPlan:
+    """Many tables' op batches in one persistent launch per phase, captured
+    into a CUDA graph.  ``items``: iterables of (table, kind, keys, vals,
+    vals_out, status_out, phase[, op]) with CUDA tensors (or None)."""
+
+    def __init__(self, items):
+        arr = (_lib.WsBatchItem * len(items))()
+        self._keep = []
+        for i, it in enumerate(items):
+            table, kind, keys, vals, vals_out, status_out, phase = it[:7]
+            op = it[7] if len(it) > 7 else 0
+            op = UPSERT_OPS[op] if isinstance(op, str) else int(op)
+            self._keep.append((table, keys, vals, vals_out, status_out))
+            arr[i] = _lib.WsBatchItem(table.handle.value if hasattr(table.handle, "value") else table.handle,
+                                      int(kind), op, int(phase), 0, _ptr(keys, 8), _ptr(vals, 8),
+                                      _ptr(vals_out, 8), _ptr(status_out), _numel(keys))
+        h = ctypes.c_void_p()
+        _check(lib().ws_batch_plan_create(arr, len(items), ctypes.byref(h)), "ws_batch_plan_create")
+        self._h = h
+        self._device = items[0][0].device
+
+    def launch(self, stream=None):
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream(self._device)
+        _check(lib().ws_batch_plan_launch(self._h, ctypes.c_void_p(s.cuda_stream)), "ws_batch_plan_launch")
+
+    def info(self):
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(lib().ws_batch_plan_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "ws_batch_plan_info")
+        return {"phases": a.value, "chunks": b.value, "fallback_items": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ws_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -28,6 +28,13 @@ class WsInfo(ctypes.Structure):
                 ("metadata", ctypes.c_int32), ("device", ctypes.c_int32), ("never_erased", ctypes.c_int32)]
 
 
+class WsBatchItem(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_void_p), ("kind", ctypes.c_int32), ("op", ctypes.c_int32),
+                ("phase", ctypes.c_int32), ("reserved", ctypes.c_int32), ("keys", ctypes.c_void_p),
+                ("vals", ctypes.c_void_p), ("vals_out", ctypes.c_void_p), ("status_out", ctypes.c_void_p),
+                ("n", ctypes.c_uint64)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "ws_table_create": (st, [u64, i32, i32, ctypes.POINTER(vp)]),
@@ -53,8 +60,14 @@ SIGNATURES = {
                            ctypes.POINTER(ctypes.c_uint64)]),
     "ws_num_buckets": (st, [vp, ctypes.POINTER(ctypes.c_uint64)]),
     "ws_primary_bucket": (st, [vp, vp, vp, u64, vp]),
+    "ws_rehash": (st, [vp, vp, vp, vp]),
     "ws_dump": (st, [vp, vp, vp]),
     "ws_debug_fill_locks": (st, [vp, i32, vp]),
+    "ws_batch_plan_create": (st, [ctypes.POINTER(WsBatchItem), u64, ctypes.POINTER(vp)]),
+    "ws_batch_plan_launch": (st, [vp, vp]),
+    "ws_batch_plan_info": (st, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64)]),
+    "ws_batch_plan_destroy": (st, [vp]),
     "ws_cuda_error_string": (ctypes.c_char_p, []),
     "ws_status_string": (ctypes.c_char_p, [i32]),
     "ws_version": (u32, []),

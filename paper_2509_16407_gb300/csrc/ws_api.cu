@@ -5,13 +5,9 @@
 #include <cstring>
 #include <new>
 
-#include "../../include/warpspeed.h"
-#include "ws_kernels.cuh"
+#include "ws_internal.h"
 
-using ws::u64;
-using ws::u8;
-
-namespace {
+namespace wsi {
 
 thread_local char g_cuda_err[256] = "no error";
 
@@ -19,62 +15,20 @@ void note_cuda(cudaError_t e, const char* where) {
   std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
 }
 
-#define WS_CUDA(call)                        \
-  do {                                       \
-    cudaError_t e_ = (call);                 \
-    if (e_ != cudaSuccess) {                 \
-      note_cuda(e_, #call);                  \
-      return WS_ERR_CUDA;                    \
-    }                                        \
-  } while (0)
+}  // namespace wsi
+
+using namespace wsi;
+
+namespace {
 
 constexpr u64 kSeed1 = 0x243f6a8885a308d3ull;  // hex digits of pi: fixed, documented seeds
 constexpr u64 kSeed2 = 0x13198a2e03707344ull;
 constexpr uint32_t kDefaultProbe = 80;
 constexpr uint32_t kDefaultSpin = 1u << 16;  // attempts; each costs a probe + <= 1 us back-off
-constexpr u64 kStageOps = 1ull << 22;
-constexpr int kDefaultPrefetch = 0;  // L2 prefetch mode (see WS_OPT_PREFETCH)  // ops per staging chunk (host-buffer path)
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    int cur = -1;
-    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev) {
-      prev = cur;
-      cudaSetDevice(dev);
-    }
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-// Double-buffered staging for host batch buffers: H2D copies on one stream,
-// kernels on the caller's stream, D2H copies on a third, chained by events.
-struct Staging {
-  u64 cap = 0;
-  u64* keys[2] = {nullptr, nullptr};
-  u64* vals[2] = {nullptr, nullptr};
-  u64* out[2] = {nullptr, nullptr};
-  u8* ops[2] = {nullptr, nullptr};
-  u8* st[2] = {nullptr, nullptr};
-  cudaStream_t h2d = nullptr, d2h = nullptr;
-  cudaEvent_t in_ready[2] = {nullptr, nullptr}, k_done[2] = {nullptr, nullptr},
-              out_done[2] = {nullptr, nullptr};
-};
+constexpr u64 kStageOps = 1ull << 22;  // ops per staging chunk (host-buffer path)
+constexpr int kDefaultPrefetch = 0;  // L2 prefetch mode (see WS_OPT_PREFETCH)
 
 }  // namespace
-
-struct ws_table {
-  ws::TableView tv;
-  u64 nb = 0, B = 0, S = 0;
-  int T = 0, scheme = 0, meta = 0, device = 0, num_sms = 0;
-  uint32_t pmax = 0, spin = 0;
-  int never_erased = 1;
-  u64 bytes = 0;
-  cudaStream_t last_stream = nullptr;
-  Staging* stage = nullptr;
-};
 
 namespace {
 
@@ -140,9 +94,9 @@ ws_status ensure_staging(ws_table* t) {
   return WS_OK;
 }
 
-enum { PTR_NULL = 0, PTR_DEVICE = 1, PTR_HOST = 2, PTR_OTHER_DEVICE = 3 };
+}  // namespace
 
-int classify(const void* p, int device) {
+int wsi::classify(const void* p, int device) {
   if (!p) return PTR_NULL;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
@@ -154,10 +108,14 @@ int classify(const void* p, int device) {
   return PTR_HOST;
 }
 
+namespace {
+
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 
-cudaError_t dispatch(const ws_table* t, const ws::TableView& tv, const ws::BatchArgs& a, int kind,
-                     cudaStream_t s) {
+}  // namespace
+
+cudaError_t wsi::dispatch(const ws_table* t, const ws::TableView& tv, const ws::BatchArgs& a, int kind,
+                          cudaStream_t s) {
   const int B = (int)t->B, T = t->T;
   if (t->scheme == WS_DOUBLE)
     return t->meta ? ws::launch_double_meta(B, T, tv, a, kind, s, t->num_sms)
@@ -165,6 +123,8 @@ cudaError_t dispatch(const ws_table* t, const ws::TableView& tv, const ws::Batch
   return t->meta ? ws::launch_p2_meta(B, T, tv, a, kind, s, t->num_sms)
                  : ws::launch_p2_plain(B, T, tv, a, kind, s, t->num_sms);
 }
+
+namespace {
 
 ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t* keys_in,
                     const uint64_t* vals_in, uint64_t* vals_out_in, u8* status_out, u64 n, cudaStream_t s) {
@@ -193,7 +153,7 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
 
   const bool any_host = pk == PTR_HOST || pv == PTR_HOST || po == PTR_HOST || pvo == PTR_HOST || pst == PTR_HOST;
   if (!any_host) {
-    ws::BatchArgs a{keys, vals, ops, vals_out, status_out, n, op};
+    ws::BatchArgs a{keys, vals, ops, vals_out, status_out, n, op, 1, 0};
     WS_CUDA(dispatch(t, tv, a, kind, s));
     return WS_OK;
   }
@@ -227,7 +187,7 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
     WS_CUDA(cudaStreamWaitEvent(s, g.out_done[b], 0));
     u64* vo = vals_out ? (pvo == PTR_HOST ? g.out[b] : vals_out + off) : nullptr;
     u8* so = status_out ? (pst == PTR_HOST ? g.st[b] : status_out + off) : nullptr;
-    ws::BatchArgs a{kp, vp, op_p, vo, so, m, op};
+    ws::BatchArgs a{kp, vp, op_p, vo, so, m, op, 1, 0};
     WS_CUDA(dispatch(t, tv, a, kind, s));
     WS_CUDA(cudaEventRecord(g.k_done[b], s));
     if (host_out) {
@@ -520,6 +480,21 @@ ws_status ws_primary_bucket(ws_table* t, const uint64_t* keys, uint64_t* out, ui
   }
   if (pk == PTR_HOST) WS_CUDA(cudaFreeAsync(dk, s));
   if (pk == PTR_HOST || po == PTR_HOST) WS_CUDA(cudaStreamSynchronize(s));
+  return WS_OK;
+}
+
+ws_status ws_rehash(ws_table* src, ws_table* dst, uint8_t* status_out, ws_stream stream) {
+  if (!src || !dst || src == dst || src->device != dst->device) return WS_ERR_INVALID;
+  DeviceGuard guard(dst->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (src->last_stream != s) WS_CUDA(cudaStreamSynchronize(src->last_stream));
+  // The source's slot array is the input: keys at stride 2, values right after.
+  const u64* base = reinterpret_cast<const u64*>(src->tv.slots);
+  ws::BatchArgs a{base, base + 1, nullptr, nullptr, status_out, src->S, ws::OP_INSERT, 2, ws::BATCH_SKIP_SENTINELS};
+  ws::TableView tv = dst->tv;
+  tv.shortcut = dst->never_erased;
+  dst->last_stream = s;
+  WS_CUDA(dispatch(dst, tv, a, ws::KIND_UPSERT, s));
   return WS_OK;
 }
 

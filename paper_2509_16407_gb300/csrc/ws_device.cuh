@@ -67,8 +67,11 @@ struct BatchArgs {
   u64* vals_out;
   u8* status_out;
   u64 n;
-  int op;  // upsert callback for KIND_UPSERT
+  int op;          // upsert callback for KIND_UPSERT
+  u32 key_stride;  // elements between consecutive keys / values (0 or 1: dense; 2: a slot array)
+  u32 flags;       // BATCH_SKIP_SENTINELS: sentinel keys are skipped silently (rehash of a slot array)
 };
+enum { BATCH_SKIP_SENTINELS = 1 };
 
 // -------------------------------------------------------------------------
 // Hashing.  The paper does not fix its hash functions; this build uses the

@@ -1,0 +1,73 @@
+// ws_internal.h -- host-side table object shared by the C-ABI units.
+#pragma once
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/warpspeed.h"
+#include "ws_kernels.cuh"
+
+namespace wsi {
+
+using ws::u64;
+using ws::u8;
+using ws::u32;
+
+// Double-buffered staging for host batch buffers: H2D copies on one stream,
+// kernels on the caller's stream, D2H copies on a third, chained by events.
+struct Staging {
+  u64 cap = 0;
+  u64* keys[2] = {nullptr, nullptr};
+  u64* vals[2] = {nullptr, nullptr};
+  u64* out[2] = {nullptr, nullptr};
+  u8* ops[2] = {nullptr, nullptr};
+  u8* st[2] = {nullptr, nullptr};
+  cudaStream_t h2d = nullptr, d2h = nullptr;
+  cudaEvent_t in_ready[2] = {nullptr, nullptr}, k_done[2] = {nullptr, nullptr},
+              out_done[2] = {nullptr, nullptr};
+};
+
+void note_cuda(cudaError_t e, const char* where);
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev) {
+      prev = cur;
+      cudaSetDevice(dev);
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+#define WS_CUDA(call)                        \
+  do {                                       \
+    cudaError_t e_ = (call);                 \
+    if (e_ != cudaSuccess) {                 \
+      ::wsi::note_cuda(e_, #call);           \
+      return WS_ERR_CUDA;                    \
+    }                                        \
+  } while (0)
+
+}  // namespace wsi
+
+struct ws_table {
+  ws::TableView tv;
+  wsi::u64 nb = 0, B = 0, S = 0;
+  int T = 0, scheme = 0, meta = 0, device = 0, num_sms = 0;
+  uint32_t pmax = 0, spin = 0;
+  int never_erased = 1;
+  wsi::u64 bytes = 0;
+  cudaStream_t last_stream = nullptr;
+  wsi::Staging* stage = nullptr;
+};
+
+namespace wsi {
+// Launch one single-table batch kernel for the table's configuration.
+cudaError_t dispatch(const ws_table* t, const ws::TableView& tv, const ws::BatchArgs& a, int kind, cudaStream_t s);
+// 1 device pointer on `device`, 2 host, 3 another device, 0 null.
+int classify(const void* p, int device);
+enum { PTR_NULL = 0, PTR_DEVICE = 1, PTR_HOST = 2, PTR_OTHER_DEVICE = 3 };
+}  // namespace wsi

@@ -341,6 +341,9 @@ struct TileOps {
   }
 
   // Reads the candidate slots of a tag match mask; true if one holds K.
+  // The leader lane reads each candidate and broadcasts the pair, so every
+  // lane of the tile takes the same branch even while another tile rewrites
+  // the slot (separate per-lane reads could disagree and split the tile).
   // With WAIT (lock-free inserts, where no erase runs concurrently) a slot
   // whose tag is claimed but whose pair is not stored yet (key EMPTY/TOMB) is
   // re-read until the claimer's release store lands, so a same-key inserter
@@ -353,19 +356,15 @@ struct TileOps {
       mm &= mm - 1;
       const u64 si = b * 32 + (u64)q;
       u64 k, v;
-      ptx::ld_slot(tv.slots + si, k, v);  // same address on every lane: one request
+      read_pair(tv, c, si, k, v);
       if (WAIT) {
-        k = c.shfl(k, 0);
-        v = c.shfl(v, 0);
         for (u32 n = 0; k == KEY_EMPTY || k == KEY_TOMB; ++n) {
           if (n >= tv.spin_limit) {
             *stuck = true;
             break;
           }
           __nanosleep(64);
-          ptx::ld_slot(tv.slots + si, k, v);
-          k = c.shfl(k, 0);
-          v = c.shfl(v, 0);
+          read_pair(tv, c, si, k, v);
         }
       }
       if (k == K) {
@@ -375,6 +374,16 @@ struct TileOps {
       }
     }
     return false;
+  }
+
+  // One slot read by the leader lane, broadcast to the tile (tile-uniform).
+  __device__ static __forceinline__ void read_pair(const TableView& tv, const TileCtx<T>& c, u64 si, u64& k,
+                                                   u64& v) {
+    k = 0;
+    v = 0;
+    if (c.tl == 0) ptx::ld_slot(tv.slots + si, k, v);
+    k = c.shfl(k, 0);
+    v = c.shfl(v, 0);
   }
 
   // Probe cost with metadata: a tag line read is 64 B (2 sectors, 1 line);
@@ -397,7 +406,7 @@ struct TileOps {
           seen &= seen - 1;
           ++nc;
           u64 kk, vv;
-          ptx::ld_slot(tv.slots + b * 32 + (u64)q, kk, vv);
+          read_pair(tv, c, b * 32 + (u64)q, kk, vv);
           if (kk == K) break;
         }
         *sectors += 2 + nc;
@@ -711,11 +720,12 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
   const int pf_method = (KIND == KIND_PROBE) ? 0 : (tv.prefetch & 3);
   const bool pf_lead = (tv.prefetch & 4) != 0;
   u64 ch = (u64)blockIdx.x * kWarps + w;
+  const u64 ks = a.key_stride ? a.key_stride : 1;
   // keys of the chunk about to be staged (prefetched one chunk ahead with pf_lead)
   u64 next_key = 0;
   if (ch < nchunks) {
     const u64 gi0 = ch * 32 + lane;
-    next_key = gi0 < a.n ? a.keys[gi0] : 0;
+    next_key = gi0 < a.n ? a.keys[gi0 * ks] : 0;
     if (pf_method && gi0 < a.n) Ops::prefetch_key(tv, next_key, pf_method);
   }
   for (; ch < nchunks; ch += stride) {
@@ -723,12 +733,12 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
     const u64 gi = base + lane;
     const bool inb = gi < a.n;
     s_key[w][lane] = next_key;
-    if (KIND == KIND_UPSERT || KIND == KIND_MIXED) s_val[w][lane] = (inb && a.vals) ? a.vals[gi] : 0;
+    if (KIND == KIND_UPSERT || KIND == KIND_MIXED) s_val[w][lane] = (inb && a.vals) ? a.vals[gi * ks] : 0;
     if (KIND == KIND_MIXED) s_op[w][lane] = inb ? a.ops[gi] : 0;
     {
       const u64 nch = ch + stride;
       const u64 ngi = nch * 32 + lane;
-      next_key = (nch < nchunks && ngi < a.n) ? a.keys[ngi] : 0;
+      next_key = (nch < nchunks && ngi < a.n) ? a.keys[ngi * ks] : 0;
       if (pf_method && pf_lead && nch < nchunks && ngi < a.n) Ops::prefetch_key(tv, next_key, pf_method);
     }
     __syncwarp();
@@ -744,7 +754,10 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
       } else if (KIND == KIND_PROBE) {
         st = Ops::do_probe(tv, c, K, out);
       } else if (KIND == KIND_UPSERT) {
-        st = Ops::template do_upsert<true>(tv, c, K, s_val[w][j], a.op, dcount);
+        if ((a.flags & BATCH_SKIP_SENTINELS) && is_sentinel(K))
+          st = ST_MISS;  // an empty / erased slot of the source table
+        else
+          st = Ops::template do_upsert<true>(tv, c, K, s_val[w][j], a.op, dcount);
       } else if (KIND == KIND_ERASE) {
         st = Ops::do_erase(tv, c, K, out, dcount);
       } else {

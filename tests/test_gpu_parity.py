@@ -420,3 +420,29 @@ def test_host_buffers_match_device_path(ws, oracle_mod):
     want, wst = om.query(q)
     assert (va == want).all() and (qa == wst).all()
     assert ta.count() == tb.count() == n
+
+
+# --------------------------------------------------------------------------
+# growth: rehash a table's live pairs into a larger one (any design)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme,meta", DESIGNS, ids=DESIGN_IDS)
+def test_rehash_into_larger_table(ws, oracle_mod, scheme, meta):
+    src = ws.Table(1 << 14, scheme, meta)
+    keys = W.distinct_keys(123, int(0.8 * (1 << 14)))
+    vals = W.splitmix64(124, keys.size)
+    om = oracle_mod.OracleMap()
+    src.insert(dev(keys), dev(vals))
+    om.insert(keys, vals)
+    src.erase(dev(keys[::3]))
+    om.erase(keys[::3])
+    for dscheme, dmeta in DESIGNS:
+        dst = ws.Table(1 << 16, dscheme, dmeta)
+        st = host(src.rehash_into(dst, return_status=True))
+        assert (st == ws.INSERTED).sum() == om.count() and ((st == ws.INSERTED) | (st == ws.MISS)).all()
+        assert dst.count() == om.count()
+        gk, gv = _map_state(dst)
+        okk, ov = om.items()
+        assert (gk == okk).all() and (gv == ov).all()
+        check_layout(oracle_mod, dst, om.count())
+        assert dst.last_error()["status"] == 0
+        dst.close()
