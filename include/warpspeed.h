@@ -130,11 +130,12 @@ ws_status ws_set_tile(ws_table* t, int tile);
 ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
 
 /* Tuning options (affect speed only, never results).
- *  WS_OPT_PREFETCH: L2 prefetch of each op's first bucket(s) (double hashing: b_0;
- *  two-choice: b_0 and b_1; metadata: their tag lines) by one lane per op before the
- *  tiles probe.  Bits 0-1: 0 off, 1 per-line prefetch, 2 bulk-range prefetch; bit 2:
- *  issue the prefetches one warp chunk ahead. */
-enum { WS_OPT_PREFETCH = 1 };
+ *  WS_OPT_PRELOAD (default 1): before a warp's tiles probe, each lane copies its
+ *  op's first probe -- the first 128-byte line of the primary bucket, or with
+ *  metadata the bucket's tag line and first tag-matching slot -- into shared
+ *  memory with asynchronous copies, so 32 first probes per warp are in flight
+ *  at once.  0 reads everything with plain loads. */
+enum { WS_OPT_PRELOAD = 1 };
 ws_status ws_set_option(ws_table* t, int option, int64_t value);
 
 /* Insert-if-unique (§5.1 Upsert with the empty callback).  status_out: per-op

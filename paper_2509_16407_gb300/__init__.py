@@ -143,9 +143,9 @@ class Table:
     def set_spin_limit(self, spins: int):
         _check(lib().ws_set_spin_limit(self._h, int(spins)), "ws_set_spin_limit")
 
-    def set_prefetch(self, mode: int):
-        """L2 prefetch of first buckets: 0 off, 1 line, 2 bulk range; +4 one chunk ahead."""
-        _check(lib().ws_set_option(self._h, 1, int(mode)), "ws_set_option")
+    def set_preload(self, on: bool):
+        """First-probe preload into shared memory (on by default)."""
+        _check(lib().ws_set_option(self._h, 1, int(bool(on))), "ws_set_option")
 
     def clear(self, stream=None):
         _check(lib().ws_clear(self._h, self._stream(stream)), "ws_clear")

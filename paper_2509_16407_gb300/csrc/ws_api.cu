@@ -26,7 +26,7 @@ constexpr u64 kSeed2 = 0x13198a2e03707344ull;
 constexpr uint32_t kDefaultProbe = 80;
 constexpr uint32_t kDefaultSpin = 1u << 16;  // attempts; each costs a probe + <= 1 us back-off
 constexpr u64 kStageOps = 1ull << 22;  // ops per staging chunk (host-buffer path)
-constexpr int kDefaultPrefetch = 0;  // L2 prefetch mode (see WS_OPT_PREFETCH)
+constexpr int kDefaultPreload = 1;  // first-probe preload (see WS_OPT_PRELOAD)
 
 }  // namespace
 
@@ -288,7 +288,7 @@ ws_status ws_table_create_ex(const ws_config* cfg, ws_table** out) {
   tv.pmax = t->pmax;
   tv.spin_limit = t->spin;
   tv.shortcut = 1;
-  tv.prefetch = kDefaultPrefetch;
+  tv.preload = kDefaultPreload;
   cudaError_t e = cudaMemset(tv.slots, 0, t->S * sizeof(ws::Slot));
   if (e == cudaSuccess && meta) e = cudaMemset(tv.tags, 0, t->S * 2);
   if (e == cudaSuccess) e = cudaMemset(tv.locks, 0, lock_words * 4);
@@ -365,9 +365,9 @@ ws_status ws_set_tile(ws_table* t, int tile) {
 ws_status ws_set_option(ws_table* t, int option, int64_t value) {
   if (!t) return WS_ERR_INVALID;
   switch (option) {
-    case WS_OPT_PREFETCH:
-      if (value < 0 || value > 6 || (value & 3) == 3) return WS_ERR_INVALID;
-      t->tv.prefetch = (int)value;
+    case WS_OPT_PRELOAD:
+      if (value != 0 && value != 1) return WS_ERR_INVALID;
+      t->tv.preload = (int)value;
       return WS_OK;
   }
   return WS_ERR_INVALID;

@@ -57,7 +57,7 @@ struct TableView {
   u32 pmax;       // double hashing: buckets a probe sequence may visit (<= nb)
   u32 spin_limit; // lock attempts before giving up
   int shortcut;   // P2: no erase ever ran, so the primary-fill shortcut is exact
-  int prefetch;   // L2 prefetch of first buckets: bits 0-1 method (0 off, 1 line, 2 bulk), bit 2 lead one chunk
+  int preload;    // stage each op's first probe into shared memory with async copies (1) or not (0)
 };
 
 struct BatchArgs {
@@ -181,13 +181,15 @@ __device__ __forceinline__ void st_u64_relaxed(u64* p, u64 v) {
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// L2 prefetch of one 128-byte line, and of a 16-byte-multiple range through
-// the bulk-copy unit.
-__device__ __forceinline__ void prefetch_line_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+// Asynchronous 16-byte global -> shared copy through L2 (cp.async.cg): the
+// first-probe snapshot of an op lands in shared memory without holding
+// registers, so a warp keeps all 32 of its ops' first probes in flight.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const u32 d = (u32)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
 }
-__device__ __forceinline__ void prefetch_bulk_l2(const void* p, u32 bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 // Tag loads of 16, 8, 4 or 2 bytes (one lane's share of a 64-byte tag line).

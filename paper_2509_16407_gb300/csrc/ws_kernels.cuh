@@ -6,7 +6,8 @@
 // step is one coalesced 128-byte line per tile; for T > B one step covers
 // T/B buckets at once (the next buckets of a double-hashing sequence, or
 // both choices of a two-choice key).  Key matches, empty slots and free
-// slots are found with warp votes over the tile.
+// slots are found with warp votes over the tile, so every decision is the
+// same on all lanes of a tile.
 //
 // Probe schemes (§2.2):
 //   double hashing  b_i = (h1 + i * (h2 | 1)) mod nb, i < max_probe; a scan
@@ -19,24 +20,35 @@
 // of 16-bit tags.  A probe reads the tag line, and only slots whose tag
 // matches are read and compared against the full key, so the result is exact.
 //
+// First-probe preload.  A tile resolves its ops one after another, so with
+// plain loads only 32/T probes of a warp are in flight.  Before the tiles
+// start, each lane therefore copies the first probe of "its" op of the
+// 32-op chunk -- the first 128-byte line of b_0, or with metadata the tag
+// line of b_0 and then the first slot whose tag matches -- into shared
+// memory with cp.async, so all 32 ops' first DRAM round trips overlap.  The
+// snapshot only stands in for the first read of a lock-free probe: a query
+// answer may come from it (queried keys are not written in the same call),
+// every write is a CAS against the current slot, and everything under a
+// lock is read afresh.
+//
 // Concurrency (§4.1, §4.2):
 //   * queries take no lock; each slot is read with one 128-bit load;
 //   * an upsert first probes lock-free; a present key is updated in place
-//     with a 64-bit atomic (stability, §2.1: keys never move), so repeated
-//     upserts of a hot key never serialise on a lock;
-//   * an absent key takes the lock bit of its primary bucket b_0 (one bit
-//     per bucket in an external array), re-scans, and claims a free slot with
-//     one 128-bit CAS that publishes key and value together (metadata
-//     tables: a 16-bit CAS on the tag, then a 128-bit release store of the
-//     pair).  The lock makes same-key inserters agree on one location (the
-//     adversarial case of Fig. 2);
-//   * erase finds the key and swaps the pair for {TOMB, 0} with a 128-bit
-//     CAS (then the tag becomes TOMB).  A tombstone never turns back into
-//     EMPTY, which keeps every early-exit rule valid.
-// Every lock wait is bounded: after spin_limit attempts the op reports
-// WS_FAIL_TIMEOUT instead of spinning on.  A tile waiting for a lock keeps
-// re-probing lock-free and finishes without the lock as soon as the key
-// appears (a concurrent inserter of the same key got there first).
+//     with a 64-bit atomic (stability, §2.1: keys never move);
+//   * plain insert / upsert calls on double-hashing tables need no lock at all
+//     (no erase runs in the same call, see do_upsert);
+//   * otherwise an absent key takes the lock bit of its primary bucket b_0
+//     (one bit per bucket in an external array), re-scans, and claims a free
+//     slot with one 128-bit CAS that publishes key and value together
+//     (metadata tables: a 16-bit CAS on the tag, then a 128-bit release store
+//     of the pair).  The lock makes same-key inserters agree on one location
+//     (the adversarial case of Fig. 2);
+//   * erase swaps the pair for {TOMB, 0} with a 128-bit CAS (then the tag
+//     becomes TOMB).  A tombstone never turns back into EMPTY, which keeps
+//     every early-exit rule valid.
+// Every wait is bounded: after spin_limit attempts the op reports
+// WS_FAIL_TIMEOUT.  A tile waiting for a lock keeps re-probing lock-free and
+// finishes without the lock as soon as the key appears.
 #pragma once
 #include "ws_device.cuh"
 
@@ -58,6 +70,24 @@ struct TileCtx {
   __device__ __forceinline__ int shfl(int v, int src) const { return __shfl_sync(mask, v, src, T); }
 };
 
+template <int T>
+__device__ __forceinline__ TileCtx<T> make_tile(int lane) {
+  TileCtx<T> c;
+  c.tl = lane & (T - 1);
+  c.base = lane & ~(T - 1);
+  c.mask = (T == 32) ? 0xffffffffu : (((1u << (T & 31)) - 1u) << c.base);
+  return c;
+}
+
+// First-probe snapshot of one op (128 B, in shared memory).  Plain tables:
+// the first 8 slots of b_0.  Metadata tables: the 32 tags of b_0 in bytes
+// 0..63, the first tag-matching slot's pair in line[4], its slot index in
+// line[5].key (~0 when no tag matched).
+struct __align__(16) PreOp {
+  Slot line[8];
+};
+constexpr u64 kNoCand = ~0ull;
+
 template <int SCHEME, bool META, int B, int T>
 struct TileOps {
   static_assert(B == 8 || B == 16 || B == 32, "bucket size");
@@ -68,6 +98,7 @@ struct TileOps {
   static constexpr int SPB = (T > B) ? 1 : (B / T);  // steps per bucket
   static constexpr int TPL = 32 / T;                 // tags per lane (metadata)
   static constexpr u32 FILL_SHORTCUT = (3u * B) / 4u;
+  static constexpr int PRE_SLOTS = B < 8 ? B : 8;    // slots of b_0 in the snapshot
 
   struct Hit {
     bool found;
@@ -75,10 +106,10 @@ struct TileOps {
   };
   struct Scan {
     bool found;
-    u64 idx, val;     // where the key is (found)
+    u64 idx, val;      // where the key is (found)
     bool has_free;
-    u64 fidx, fk, fv; // free slot to claim and its observed content (tag in fk for META)
-    bool stuck;       // a wait for a claimed slot's pair ran out
+    u64 fidx, fk, fv;  // free slot to claim and its observed content (tag in fk for META)
+    bool stuck;        // a wait for a claimed slot's pair ran out
   };
 
   __device__ static __forceinline__ u32 nprobe(const TableView& tv) {
@@ -95,32 +126,40 @@ struct TileOps {
     return b1;
   }
 
-  // Bring the first bucket(s) of key K into L2 ahead of the tile that will
-  // probe them (one lane per op, so a warp has 32 ops' lines in flight while
-  // its tiles work through the ops one at a time).  Double hashing: b_0;
-  // two-choice: b_0 and b_1.  Metadata tables: the 64-byte tag lines.
-  __device__ static __forceinline__ void prefetch_one(const TableView& tv, u64 b, int method) {
+  // ----------------------------------------------------------------------
+  // First-probe preload (one lane per op; see the file comment)
+  // ----------------------------------------------------------------------
+  __device__ static __forceinline__ void preload_issue(const TableView& tv, u64 K, PreOp* p) {
+    const u64 b0 = fmix64(K ^ tv.seed1) & tv.nb_mask;
     if (META) {
-      const u16* tp = tv.tags + b * 32;
-      if (method == 2)
-        ptx::prefetch_bulk_l2(tp, 64);
-      else
-        ptx::prefetch_line_l2(tp);
-    } else {
-      const Slot* sp = tv.slots + b * B;
-      if (method == 2) {
-        ptx::prefetch_bulk_l2(sp, B * 16);
-      } else {
+      const char* src = reinterpret_cast<const char*>(tv.tags + b0 * 32);
 #pragma unroll
-        for (int l = 0; l < (B * 16) / 128; ++l) ptx::prefetch_line_l2(sp + l * 8);
-      }
+      for (int i = 0; i < 4; ++i) ptx::cp_async16(reinterpret_cast<char*>(p) + 16 * i, src + 16 * i);
+    } else {
+      const Slot* src = tv.slots + b0 * B;
+#pragma unroll
+      for (int i = 0; i < PRE_SLOTS; ++i) ptx::cp_async16(&p->line[i], src + i);
     }
   }
-  __device__ static __forceinline__ void prefetch_key(const TableView& tv, u64 K, int method) {
-    if (is_sentinel(K)) return;
-    const u64 h1 = fmix64(K ^ tv.seed1);
-    prefetch_one(tv, h1 & tv.nb_mask, method);
-    if (SCHEME == SCHEME_P2 && tv.nb_mask) prefetch_one(tv, bucket(tv, h1, fmix64(K ^ tv.seed2), 1), method);
+  // Metadata second wave: the first slot of b_0 whose tag matches K.
+  __device__ static __forceinline__ void preload_candidate(const TableView& tv, u64 K, PreOp* p) {
+    const u64 b0 = fmix64(K ^ tv.seed1) & tv.nb_mask;
+    const u16 kt = key_tag(K);
+    const u64* w = reinterpret_cast<const u64*>(p);
+    int q = -1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const u64 x = w[i];
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+        if (q < 0 && (u16)((x >> (16 * h)) & 0xffffu) == kt) q = 4 * i + h;
+    }
+    if (q >= 0) {
+      ptx::cp_async16(&p->line[4], tv.slots + b0 * 32 + (u64)q);
+      p->line[5].key = b0 * 32 + (u64)q;
+    } else {
+      p->line[5].key = kNoCand;
+    }
   }
 
   // ----------------------------------------------------------------------
@@ -131,9 +170,24 @@ struct TileOps {
   static constexpr u32 kStepSectors = LPB / 2;
   static constexpr u32 kStepLines = (LPB * 16 + 127) / 128;
 
+  // Slot read of a probe step: from the snapshot when it holds the slot.
+  __device__ static __forceinline__ void step_read(const TableView& tv, const PreOp* pre, bool first, int g,
+                                                   int sl, u64 si, bool act, u64& k, u64& v) {
+    k = KEY_RESV;
+    v = 0;
+    if (!act) return;
+    if (pre && first && g == 0 && sl < PRE_SLOTS) {
+      const Slot s = pre->line[sl];
+      k = s.key;
+      v = s.val;
+    } else {
+      ptx::ld_slot(tv.slots + si, k, v);
+    }
+  }
+
   template <bool COUNT = false>
   __device__ static Hit find_plain(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
-                                   u32* sectors = nullptr, u32* lines = nullptr) {
+                                   const PreOp* pre = nullptr, u32* sectors = nullptr, u32* lines = nullptr) {
     const u32 P = nprobe(tv);
     const int g = c.tl / LPB, j = c.tl % LPB;
     u32 occ0 = 0;
@@ -143,9 +197,10 @@ struct TileOps {
       bool ended = false;
 #pragma unroll
       for (int s = 0; s < SPB; ++s) {
-        const u64 si = b * B + (u64)(s * LPB + j);
-        u64 k = KEY_RESV, v = 0;
-        if (act) ptx::ld_slot(tv.slots + si, k, v);
+        const int sl = s * LPB + j;
+        const u64 si = b * B + (u64)sl;
+        u64 k, v;
+        step_read(tv, pre, i == 0, g, sl, si, act, k, v);
         if (COUNT) {
           const u32 nact = (u32)((P - i) < (u32)G ? (P - i) : (u32)G);
           *sectors += nact * kStepSectors;
@@ -156,8 +211,7 @@ struct TileOps {
           const int src = __ffs(hit) - 1;
           return {true, c.shfl(si, src), c.shfl(v, src)};
         }
-        if (SCHEME == SCHEME_P2 && G == 1 && i == 0)
-          occ0 += __popc(c.ballot(k != KEY_EMPTY && k != KEY_TOMB));
+        if (SCHEME == SCHEME_P2 && G == 1 && i == 0) occ0 += __popc(c.ballot(k != KEY_EMPTY && k != KEY_TOMB));
         if (c.ballot(k == KEY_EMPTY)) {
           ended = true;
           break;
@@ -172,7 +226,8 @@ struct TileOps {
     return {false, 0, 0};
   }
 
-  __device__ static Scan scan_plain(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2) {
+  __device__ static Scan scan_plain(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
+                                    const PreOp* pre) {
     Scan r;
     r.stuck = false;
     r.found = false;
@@ -186,9 +241,10 @@ struct TileOps {
         const u64 b = bucket(tv, h1, h2, act ? i + g : i);
 #pragma unroll
         for (int s = 0; s < SPB; ++s) {
-          const u64 si = b * B + (u64)(s * LPB + j);
-          u64 k = KEY_RESV, v = 0;
-          if (act) ptx::ld_slot(tv.slots + si, k, v);
+          const int sl = s * LPB + j;
+          const u64 si = b * B + (u64)sl;
+          u64 k, v;
+          step_read(tv, pre, i == 0, g, sl, si, act, k, v);
           const unsigned hit = c.ballot(k == K);
           if (hit) {
             const int src = __ffs(hit) - 1;
@@ -221,9 +277,10 @@ struct TileOps {
         const u64 b = bucket(tv, h1, h2, bi);
 #pragma unroll
         for (int s = 0; s < SPB; ++s) {
-          const u64 si = b * B + (u64)(s * LPB + j);
+          const int sl = s * LPB + j;
+          const u64 si = b * B + (u64)sl;
           u64 k, v;
-          ptx::ld_slot(tv.slots + si, k, v);
+          step_read(tv, pre, bi == 0, 0, sl, si, true, k, v);
           const unsigned hit = c.ballot(k == K);
           if (hit) {
             const int src = __ffs(hit) - 1;
@@ -252,8 +309,8 @@ struct TileOps {
       const bool act = g < (int)nbk;
       const u64 b = bucket(tv, h1, h2, act ? (u32)g : 0u);
       const u64 si = b * B + (u64)j;
-      u64 k = KEY_RESV, v = 0;
-      if (act) ptx::ld_slot(tv.slots + si, k, v);
+      u64 k, v;
+      step_read(tv, pre, true, g, j, si, act, k, v);
       const unsigned hit = c.ballot(k == K);
       if (hit) {
         const int src = __ffs(hit) - 1;
@@ -295,44 +352,36 @@ struct TileOps {
   // ----------------------------------------------------------------------
   // Metadata buckets: 32 slots, 64-byte tag line, TPL tags per lane
   // ----------------------------------------------------------------------
-  __device__ static __forceinline__ void tag_masks(const TableView& tv, const TileCtx<T>& c, u64 b,
-                                                   u16 kt, unsigned& mm, unsigned& me,
+  __device__ static __forceinline__ void tag_masks(const TableView& tv, const TileCtx<T>& c, u64 b, u16 kt,
+                                                   const PreOp* pre, unsigned& mm, unsigned& me,
                                                    unsigned& mf) {
-    const u16* tp = tv.tags + b * 32 + (u64)(c.tl * TPL);
+    const u16* tp = pre ? reinterpret_cast<const u16*>(pre) + c.tl * TPL : tv.tags + b * 32 + (u64)(c.tl * TPL);
     unsigned lm = 0, le = 0, lf = 0;
-    if (TPL == 8) {
+    u16 t[TPL];
+    if (pre) {
+#pragma unroll
+      for (int q = 0; q < TPL; ++q) t[q] = tp[q];
+    } else if (TPL == 8) {
       u64 a0, a1;
       ptx::ld_tags16(tp, a0, a1);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const u16 t = (u16)(((q < 4) ? (a0 >> (16 * q)) : (a1 >> (16 * (q - 4)))) & 0xffffu);
-        lm |= (unsigned)(t == kt) << q;
-        le |= (unsigned)(t == TAG_EMPTY) << q;
-        lf |= (unsigned)(t < 2) << q;
-      }
+      for (int q = 0; q < TPL; ++q) t[q] = (u16)(((q < 4) ? (a0 >> (16 * q)) : (a1 >> (16 * (q - 4)))) & 0xffffu);
     } else if (TPL == 4) {
       const u64 a = ptx::ld_tags8(tp);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const u16 t = (u16)((a >> (16 * q)) & 0xffffu);
-        lm |= (unsigned)(t == kt) << q;
-        le |= (unsigned)(t == TAG_EMPTY) << q;
-        lf |= (unsigned)(t < 2) << q;
-      }
+      for (int q = 0; q < TPL; ++q) t[q] = (u16)((a >> (16 * q)) & 0xffffu);
     } else if (TPL == 2) {
       const u32 a = ptx::ld_tags4(tp);
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const u16 t = (u16)((a >> (16 * q)) & 0xffffu);
-        lm |= (unsigned)(t == kt) << q;
-        le |= (unsigned)(t == TAG_EMPTY) << q;
-        lf |= (unsigned)(t < 2) << q;
-      }
+      for (int q = 0; q < TPL; ++q) t[q] = (u16)((a >> (16 * q)) & 0xffffu);
     } else {
-      const u16 t = ptx::ld_tags2(tp);
-      lm = (t == kt);
-      le = (t == TAG_EMPTY);
-      lf = (t < 2);
+      t[0] = ptx::ld_tags2(tp);
+    }
+#pragma unroll
+    for (int q = 0; q < TPL; ++q) {
+      lm |= (unsigned)(t[q] == kt) << q;
+      le |= (unsigned)(t[q] == TAG_EMPTY) << q;
+      lf |= (unsigned)(t[q] < 2) << q;
     }
     const int sh = c.tl * TPL;
     mm = __reduce_or_sync(c.mask, lm << sh);
@@ -340,23 +389,43 @@ struct TileOps {
     mf = __reduce_or_sync(c.mask, lf << sh);
   }
 
+  // One slot read by the leader lane, broadcast to the tile (tile-uniform).
+  __device__ static __forceinline__ void read_pair(const TableView& tv, const TileCtx<T>& c, u64 si, u64& k,
+                                                   u64& v) {
+    k = 0;
+    v = 0;
+    if (c.tl == 0) ptx::ld_slot(tv.slots + si, k, v);
+    k = c.shfl(k, 0);
+    v = c.shfl(v, 0);
+  }
+
   // Reads the candidate slots of a tag match mask; true if one holds K.
   // The leader lane reads each candidate and broadcasts the pair, so every
   // lane of the tile takes the same branch even while another tile rewrites
   // the slot (separate per-lane reads could disagree and split the tile).
-  // With WAIT (lock-free inserts, where no erase runs concurrently) a slot
-  // whose tag is claimed but whose pair is not stored yet (key EMPTY/TOMB) is
-  // re-read until the claimer's release store lands, so a same-key inserter
-  // cannot miss a copy being written.  *stuck reports a wait that ran out.
-  template <bool WAIT = false>
+  // The snapshot's candidate (same shared value on every lane) stands in for
+  // the first read when it is that slot.  With WAIT (lock-free inserts, where
+  // no erase runs concurrently) a slot whose tag is claimed but whose pair is
+  // not stored yet (key EMPTY/TOMB) is re-read until the claimer's release
+  // store lands, so a same-key inserter cannot miss a copy being written.
+  // *stuck reports a wait that ran out.
+  template <bool WAIT = false, bool COUNT = false>
   __device__ static __forceinline__ bool verify(const TableView& tv, const TileCtx<T>& c, u64 b, unsigned mm,
-                                                u64 K, u64& idx, u64& val, bool* stuck = nullptr) {
+                                                u64 K, const PreOp* pre, u64& idx, u64& val,
+                                                bool* stuck = nullptr, u32* nread = nullptr) {
     while (mm) {
       const int q = __ffs(mm) - 1;
       mm &= mm - 1;
       const u64 si = b * 32 + (u64)q;
       u64 k, v;
-      read_pair(tv, c, si, k, v);
+      if (pre && pre->line[5].key == si) {
+        const Slot s = pre->line[4];
+        k = s.key;
+        v = s.val;
+      } else {
+        read_pair(tv, c, si, k, v);
+      }
+      if (COUNT) ++*nread;
       if (WAIT) {
         for (u32 n = 0; k == KEY_EMPTY || k == KEY_TOMB; ++n) {
           if (n >= tv.spin_limit) {
@@ -376,44 +445,26 @@ struct TileOps {
     return false;
   }
 
-  // One slot read by the leader lane, broadcast to the tile (tile-uniform).
-  __device__ static __forceinline__ void read_pair(const TableView& tv, const TileCtx<T>& c, u64 si, u64& k,
-                                                   u64& v) {
-    k = 0;
-    v = 0;
-    if (c.tl == 0) ptx::ld_slot(tv.slots + si, k, v);
-    k = c.shfl(k, 0);
-    v = c.shfl(v, 0);
-  }
-
   // Probe cost with metadata: a tag line read is 64 B (2 sectors, 1 line);
   // each candidate slot read is one 32-byte sector of one line.
   template <bool COUNT = false>
   __device__ static Hit find_meta(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
-                                  u32* sectors = nullptr, u32* lines = nullptr) {
+                                  const PreOp* pre = nullptr, u32* sectors = nullptr, u32* lines = nullptr) {
     const u32 P = nprobe(tv);
     const u16 kt = key_tag(K);
     for (u32 i = 0; i < P; ++i) {
       const u64 b = bucket(tv, h1, h2, i);
+      const PreOp* p = (i == 0) ? pre : nullptr;
       unsigned mm, me, mf;
-      tag_masks(tv, c, b, kt, mm, me, mf);
+      tag_masks(tv, c, b, kt, p, mm, me, mf);
+      u64 idx, val;
+      u32 nc = 0;
+      const bool got = verify<false, COUNT>(tv, c, b, mm, K, p, idx, val, nullptr, &nc);
       if (COUNT) {
-        // candidates read until the key is found (at most all of them)
-        unsigned seen = mm;
-        u32 nc = 0;
-        while (seen) {
-          const int q = __ffs(seen) - 1;
-          seen &= seen - 1;
-          ++nc;
-          u64 kk, vv;
-          read_pair(tv, c, b * 32 + (u64)q, kk, vv);
-          if (kk == K) break;
-        }
         *sectors += 2 + nc;
         *lines += 1 + nc;
       }
-      u64 idx, val;
-      if (verify(tv, c, b, mm, K, idx, val)) return {true, idx, val};
+      if (got) return {true, idx, val};
       if (SCHEME == SCHEME_DOUBLE) {
         if (me) break;
       } else if (i == 0 && tv.shortcut && (u32)(32 - __popc(mf)) < FILL_SHORTCUT) {
@@ -424,7 +475,8 @@ struct TileOps {
   }
 
   template <bool WAIT = false>
-  __device__ static Scan scan_meta(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2) {
+  __device__ static Scan scan_meta(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
+                                   const PreOp* pre) {
     Scan r;
     r.stuck = false;
     r.found = false;
@@ -435,12 +487,14 @@ struct TileOps {
     if (SCHEME == SCHEME_DOUBLE) {
       for (u32 i = 0; i < P; ++i) {
         const u64 b = bucket(tv, h1, h2, i);
+        const PreOp* p = (i == 0) ? pre : nullptr;
         unsigned mm, me, mf;
-        tag_masks(tv, c, b, kt, mm, me, mf);
-        if (verify<WAIT>(tv, c, b, mm, K, r.idx, r.val, &r.stuck)) {
+        tag_masks(tv, c, b, kt, p, mm, me, mf);
+        if (verify<WAIT>(tv, c, b, mm, K, p, r.idx, r.val, &r.stuck)) {
           r.found = true;
           return r;
         }
+        if (r.stuck) return r;
         if (mf && !r.has_free) {
           const int q = __ffs(mf) - 1;
           r.has_free = true;
@@ -457,12 +511,14 @@ struct TileOps {
     bool decided0 = (P == 1);
     for (u32 bi = 0; bi < P; ++bi) {
       const u64 b = bucket(tv, h1, h2, bi);
+      const PreOp* p = (bi == 0) ? pre : nullptr;
       unsigned mm, me, mf;
-      tag_masks(tv, c, b, kt, mm, me, mf);
-      if (verify<WAIT>(tv, c, b, mm, K, r.idx, r.val, &r.stuck)) {
+      tag_masks(tv, c, b, kt, p, mm, me, mf);
+      if (verify<WAIT>(tv, c, b, mm, K, p, r.idx, r.val, &r.stuck)) {
         r.found = true;
         return r;
       }
+      if (r.stuck) return r;
       occ[bi] = (u32)(32 - __popc(mf));
       if (mf) {
         const int q = __ffs(mf) - 1;
@@ -491,21 +547,21 @@ struct TileOps {
   // ----------------------------------------------------------------------
   // Shared pieces
   // ----------------------------------------------------------------------
-  __device__ static __forceinline__ Hit find(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1,
-                                             u64 h2) {
-    if (META) return find_meta(tv, c, K, h1, h2);
-    return find_plain(tv, c, K, h1, h2);
+  __device__ static __forceinline__ Hit find(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
+                                             const PreOp* pre) {
+    if (META) return find_meta(tv, c, K, h1, h2, pre);
+    return find_plain(tv, c, K, h1, h2, pre);
   }
   template <bool WAIT = false>
-  __device__ static __forceinline__ Scan scan(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1,
-                                              u64 h2) {
-    if (META) return scan_meta<WAIT>(tv, c, K, h1, h2);
-    return scan_plain(tv, c, K, h1, h2);
+  __device__ static __forceinline__ Scan scan(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
+                                              const PreOp* pre) {
+    if (META) return scan_meta<WAIT>(tv, c, K, h1, h2, pre);
+    return scan_plain(tv, c, K, h1, h2, pre);
   }
 
   // Claim the scanned free slot for (K, V).  Leader lane writes; all learn the outcome.
-  __device__ static __forceinline__ bool claim(const TableView& tv, const TileCtx<T>& c, const Scan& r,
-                                               u64 K, u64 V) {
+  __device__ static __forceinline__ bool claim(const TableView& tv, const TileCtx<T>& c, const Scan& r, u64 K,
+                                               u64 V) {
     int ok = 0;
     if (c.tl == 0) {
       if (META) {
@@ -561,13 +617,14 @@ struct TileOps {
   }
 
   // ----------------------------------------------------------------------
-  // Operations (tile-uniform control flow; results valid on every lane)
+  // Operations (tile-uniform control flow; results valid on every lane).
+  // pre: the op's first-probe snapshot, or null.
   // ----------------------------------------------------------------------
-  __device__ static u8 do_query(const TableView& tv, const TileCtx<T>& c, u64 K, u64& out) {
+  __device__ static u8 do_query(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, const PreOp* pre,
+                                u64& out) {
     out = 0;
     if (is_sentinel(K)) return ST_BADKEY;
-    const u64 h1 = fmix64(K ^ tv.seed1), h2 = fmix64(K ^ tv.seed2);
-    const Hit h = find(tv, c, K, h1, h2);
+    const Hit h = find(tv, c, K, h1, h2, pre);
     if (!h.found) return ST_MISS;
     out = h.val;
     return ST_FOUND;
@@ -582,9 +639,9 @@ struct TileOps {
     u32 sec = 0, lin = 0;
     Hit h;
     if (META)
-      h = find_meta<true>(tv, c, K, h1, h2, &sec, &lin);
+      h = find_meta<true>(tv, c, K, h1, h2, nullptr, &sec, &lin);
     else
-      h = find_plain<true>(tv, c, K, h1, h2, &sec, &lin);
+      h = find_plain<true>(tv, c, K, h1, h2, nullptr, &sec, &lin);
     out = ((u64)lin << 32) | (u64)sec;
     return h.found ? ST_FOUND : ST_MISS;
   }
@@ -592,25 +649,29 @@ struct TileOps {
   // LOCKFREE: the caller guarantees that no erase runs in the same launch (a
   // plain insert / upsert call is one phase).
   template <bool LOCKFREE>
-  __device__ static u8 do_upsert(const TableView& tv, const TileCtx<T>& c, u64 K, u64 V, int op,
-                                 int& dcount) {
+  __device__ static u8 do_upsert(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, u64 V, int op,
+                                 const PreOp* pre, int& dcount) {
     if (is_sentinel(K)) return ST_BADKEY;
-    const u64 h1 = fmix64(K ^ tv.seed1), h2 = fmix64(K ^ tv.seed2);
     if (LOCKFREE && SCHEME == SCHEME_DOUBLE) {
       // Without erases, free slots only disappear, so every inserter of K
       // targets the first free slot of K's probe sequence: the CAS winner
       // places K and a loser's rescan finds it (with metadata, verify waits
       // out a claimed-but-unwritten slot).  No lock is needed; the lock of
       // §4.1 is for inserts racing erases (mixed batches) and for two-choice
-      // placement, whose choice depends on the moment's bucket loads.
+      // placement, whose choice depends on the moment's bucket loads.  The
+      // first scan may use the snapshot: a stale free slot only makes the
+      // CAS fail, and the rescans read afresh.
       for (int attempt = 0; attempt < 256; ++attempt) {
-        const Scan r = scan<true>(tv, c, K, h1, h2);
+        const Scan r = scan<true>(tv, c, K, h1, h2, attempt == 0 ? pre : nullptr);
         if (r.stuck) return ST_TIMEOUT;
         if (r.found) {
           if (c.tl == 0) apply(tv, r.idx, op, V);
           return ST_FOUND;
         }
-        if (!r.has_free) return ST_FULL;
+        if (!r.has_free) {
+          if (attempt == 0 && pre) continue;  // confirm a full sequence on fresh data
+          return ST_FULL;
+        }
         if (claim(tv, c, r, K, V)) {
           ++dcount;
           return ST_INSERTED;
@@ -618,7 +679,7 @@ struct TileOps {
       }
       return ST_TIMEOUT;
     }
-    const Hit h = find(tv, c, K, h1, h2);
+    const Hit h = find(tv, c, K, h1, h2, pre);
     if (h.found) {
       if (c.tl == 0) apply(tv, h.idx, op, V);
       return ST_FOUND;
@@ -631,7 +692,7 @@ struct TileOps {
     const u64 b0 = bucket(tv, h1, h2, 0);
     for (u32 tries = 0, ns = 0;;) {
       if (try_lock(tv, c, b0)) break;
-      const Hit again = find(tv, c, K, h1, h2);
+      const Hit again = find(tv, c, K, h1, h2, nullptr);
       if (again.found) {
         if (c.tl == 0) apply(tv, again.idx, op, V);
         return ST_FOUND;
@@ -641,7 +702,7 @@ struct TileOps {
     }
     u8 st = ST_TIMEOUT;
     for (int attempt = 0; attempt < 256; ++attempt) {
-      const Scan r = scan(tv, c, K, h1, h2);
+      const Scan r = scan(tv, c, K, h1, h2, nullptr);
       if (r.found) {
         if (c.tl == 0) apply(tv, r.idx, op, V);
         st = ST_FOUND;
@@ -661,13 +722,12 @@ struct TileOps {
     return st;
   }
 
-  __device__ static u8 do_erase(const TableView& tv, const TileCtx<T>& c, u64 K, u64& out,
-                                int& dcount) {
+  __device__ static u8 do_erase(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, const PreOp* pre,
+                                u64& out, int& dcount) {
     out = 0;
     if (is_sentinel(K)) return ST_BADKEY;
-    const u64 h1 = fmix64(K ^ tv.seed1), h2 = fmix64(K ^ tv.seed2);
     for (int attempt = 0; attempt < 256; ++attempt) {
-      const Hit h = find(tv, c, K, h1, h2);
+      const Hit h = find(tv, c, K, h1, h2, attempt == 0 ? pre : nullptr);
       if (!h.found) return ST_MISS;
       int ok = 0;
       if (c.tl == 0) {
@@ -682,115 +742,371 @@ struct TileOps {
     }
     return ST_TIMEOUT;
   }
+
+  // One op of the mixed codes (queries, upserts under the locked path, erases).
+  __device__ static __forceinline__ u8 do_mixed(const TableView& tv, const TileCtx<T>& c, u8 code, u64 K, u64 h1,
+                                                u64 h2, u64 V, const PreOp* pre, u64& out, int& dcount) {
+    out = 0;
+    switch (code) {
+      case MX_QUERY: return do_query(tv, c, K, h1, h2, pre, out);
+      case MX_INSERT: return do_upsert<false>(tv, c, K, h1, h2, V, OP_INSERT, pre, dcount);
+      case MX_ADD: return do_upsert<false>(tv, c, K, h1, h2, V, OP_ADD, pre, dcount);
+      case MX_MAX: return do_upsert<false>(tv, c, K, h1, h2, V, OP_MAX, pre, dcount);
+      case MX_REPLACE: return do_upsert<false>(tv, c, K, h1, h2, V, OP_REPLACE, pre, dcount);
+      case MX_ERASE: return do_erase(tv, c, K, h1, h2, pre, out, dcount);
+      default: return ST_BADKEY;
+    }
+  }
+
+  // ----------------------------------------------------------------------
+  // Lane fast path: one lane settles its own op from the snapshot alone --
+  // a hit, a miss proven by an EMPTY slot (or the two-choice shortcut), or
+  // a claim / erase by one 128-bit CAS.  Returns true when settled.
+  // *fresh becomes false when the lane tried a CAS that failed: the table
+  // moved on, so the tile path must not reuse the snapshot.
+  // ----------------------------------------------------------------------
+  struct Snap {
+    int hit;         // slot of K in the snapshot, -1 if none
+    int ffree;       // first free slot (plain) / first free tag (metadata), -1 if none
+    bool ffree_empty;
+    bool empty;      // an EMPTY slot / tag seen: no key sits past it in b_0
+    u32 occ;         // occupied slots of b_0 (exact when `empty`)
+    bool unsure;     // metadata: a tag match that the snapshot cannot settle
+  };
+
+  __device__ static __forceinline__ Snap snap_of(const PreOp& p, u64 K) {
+    Snap sn;
+    sn.hit = -1;
+    sn.ffree = -1;
+    sn.ffree_empty = false;
+    sn.empty = false;
+    sn.occ = 0;
+    sn.unsure = false;
+    if (!META) {
+#pragma unroll
+      for (int s = 0; s < PRE_SLOTS; ++s) {
+        const u64 k = p.line[s].key;
+        if (k == K && sn.hit < 0) sn.hit = s;
+        const bool fr = (k == KEY_EMPTY || k == KEY_TOMB);
+        if (fr && sn.ffree < 0) {
+          sn.ffree = s;
+          sn.ffree_empty = (k == KEY_EMPTY);
+        }
+        sn.empty |= (k == KEY_EMPTY);
+        sn.occ += fr ? 0u : 1u;
+      }
+    } else {
+      const u16 kt = key_tag(K);
+      const u64* w = reinterpret_cast<const u64*>(&p);
+      int nmatch = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const u64 x = w[i];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+          const u16 t = (u16)((x >> (16 * h)) & 0xffffu);
+          const int q = 4 * i + h;
+          nmatch += (t == kt);
+          if (t < 2 && sn.ffree < 0) {
+            sn.ffree = q;
+            sn.ffree_empty = (t == TAG_EMPTY);
+          }
+          sn.empty |= (t == TAG_EMPTY);
+          sn.occ += (t < 2) ? 0u : 1u;
+        }
+      }
+      if (nmatch > 0) {
+        const u64 ck = p.line[4].key;
+        if (ck == K)
+          sn.hit = 0;  // the candidate pair is K's
+        else if (nmatch > 1 || ck == KEY_EMPTY || ck == KEY_TOMB)
+          sn.unsure = true;  // more candidates, or a claimed slot not written yet
+      }
+    }
+    return sn;
+  }
+
+  // Slot index and pair of the snapshot hit.
+  __device__ static __forceinline__ void hit_pair(const PreOp& p, const Snap& sn, u64 b0, u64& idx, u64& val) {
+    if (META) {
+      idx = p.line[5].key;
+      val = p.line[4].val;
+    } else {
+      idx = b0 * B + (u64)sn.hit;
+      val = p.line[sn.hit].val;
+    }
+  }
+
+  // Does the snapshot prove K absent (for a lock-free probe)?
+  __device__ static __forceinline__ bool snap_absent(const TableView& tv, const Snap& sn) {
+    if (sn.hit >= 0 || sn.unsure || !sn.empty) return false;
+    if (SCHEME == SCHEME_DOUBLE) return true;
+    return tv.shortcut && sn.occ < FILL_SHORTCUT && tv.nb_mask != 0;
+  }
+
+  __device__ static __forceinline__ bool lane_query(const TableView& tv, const PreOp& p, u64 K, u64 b0, u64& out,
+                                                    u8& st) {
+    const Snap sn = snap_of(p, K);
+    if (sn.hit >= 0) {
+      u64 idx;
+      hit_pair(p, sn, b0, idx, out);
+      st = ST_FOUND;
+      return true;
+    }
+    if (snap_absent(tv, sn)) {
+      out = 0;
+      st = ST_MISS;
+      return true;
+    }
+    return false;
+  }
+
+  // Upsert: a hit is updated in place; with LOCKFREE double hashing an absent
+  // key is claimed into the first free slot of b_0 (it precedes the EMPTY
+  // slot that ended the existence scan, so it is the first free slot of the
+  // probe sequence).
+  template <bool LOCKFREE>
+  __device__ static __forceinline__ bool lane_upsert(const TableView& tv, const PreOp& p, u64 K, u64 b0, u64 V, int op,
+                                                     u8& st, int& dcount, bool& fresh) {
+    const Snap sn = snap_of(p, K);
+    if (sn.hit >= 0) {
+      u64 idx, v;
+      hit_pair(p, sn, b0, idx, v);
+      apply(tv, idx, op, V);
+      st = ST_FOUND;
+      return true;
+    }
+    if (!(LOCKFREE && SCHEME == SCHEME_DOUBLE) || !snap_absent(tv, sn) || sn.ffree < 0) return false;
+    const u64 fi = b0 * B + (u64)sn.ffree;
+    bool ok;
+    if (META) {
+      const u16 expect = sn.ffree_empty ? TAG_EMPTY : TAG_TOMB;
+      ok = ptx::cas_tag(tv.tags + fi, expect, key_tag(K)) == expect;
+      if (ok) ptx::st_slot_release(tv.slots + fi, K, V);
+    } else {
+      const Slot o = p.line[sn.ffree];
+      ok = ptx::cas_slot(tv.slots + fi, o.key, o.val, K, V);
+    }
+    if (!ok) {
+      fresh = false;
+      return false;
+    }
+    ++dcount;
+    st = ST_INSERTED;
+    return true;
+  }
+
+  __device__ static __forceinline__ bool lane_erase(const TableView& tv, const PreOp& p, u64 K, u64 b0, u64& out,
+                                                    u8& st, int& dcount, bool& fresh) {
+    const Snap sn = snap_of(p, K);
+    if (sn.hit >= 0) {
+      u64 idx, v;
+      hit_pair(p, sn, b0, idx, v);
+      if (!ptx::cas_slot(tv.slots + idx, K, v, KEY_TOMB, 0)) {
+        fresh = false;
+        return false;
+      }
+      if (META) ptx::st_tag_release(tv.tags + idx, TAG_TOMB);
+      out = v;
+      --dcount;
+      st = ST_FOUND;
+      return true;
+    }
+    if (snap_absent(tv, sn)) {
+      out = 0;
+      st = ST_MISS;
+      return true;
+    }
+    return false;
+  }
 };
 
+// Failure counters for a finished op (leader lane).
+__device__ __forceinline__ void count_failure(const TableView& tv, u8 st) {
+  if (st >= ST_FULL) {
+    u64* ctr = st == ST_FULL ? &tv.ctr->n_full : st == ST_TIMEOUT ? &tv.ctr->n_timeout : &tv.ctr->n_badkey;
+    atomicAdd((unsigned long long*)ctr, 1ull);
+  }
+}
+
 // -------------------------------------------------------------------------
-// The batch kernel.  Each warp takes chunks of 32 consecutive ops (grid
-// stride); the chunk's keys/values/op codes are staged through shared memory
-// with coalesced loads, tile t of the warp serves ops t*T .. t*T+T-1 of the
-// chunk one after another, and results go back through shared memory as
-// coalesced stores.  Count deltas are summed per block and added with one
-// atomic per block.
+// One warp serves a chunk of up to 32 consecutive ops.
+//  1. Stage: lane j loads op j's key (value, op code) with coalesced loads and
+//     hashes it once; keys and hashes go to shared memory.
+//  2. Preload: the first probe of all 32 ops is copied into shared memory
+//     (cp.async; four ops' 128-byte lines per instruction, so each copy
+//     instruction is coalesced), and with metadata a second wave fetches
+//     each op's first tag-matching slot.
+//  3. Lane fast path: lane j settles op j from the snapshot when it can.
+//  4. Tiles serve the ops left over, dealt round-robin, with the cooperative
+//     probe (snapshot reused unless a lane CAS showed it stale).
+//  5. Results leave through shared memory as coalesced stores.
 // -------------------------------------------------------------------------
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
+struct WarpSmem {
+  u64 key[32], val[32], out[32], h1[32], h2[32];
+  u8 op[32], st[32], fresh[32], pad[32];
+  PreOp pre[32];
+};
+
+enum { FLAG_SNAP = 1, FLAG_DONE = 2 };
+
+template <int SCHEME, bool META, int B, int T, int KIND>
+__device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& a, int upsert_op, bool lockfree,
+                                          u64 base, WarpSmem& sm, int lane) {
+  using Ops = TileOps<SCHEME, META, B, T>;
+  const u64 ks = a.key_stride ? a.key_stride : 1;
+  const u64 gi = base + lane;
+  const bool inb = gi < a.n;
+  const u64 K = inb ? a.keys[gi * ks] : 0;
+  const u64 V = ((KIND == KIND_UPSERT || KIND == KIND_MIXED) && inb && a.vals) ? a.vals[gi * ks] : 0;
+  const u8 code = (KIND == KIND_MIXED && inb) ? a.ops[gi] : 0;
+  const u64 h1 = fmix64(K ^ tv.seed1), h2 = fmix64(K ^ tv.seed2);
+  const u64 b0 = h1 & tv.nb_mask;
+  sm.key[lane] = K;
+  sm.val[lane] = V;
+  sm.op[lane] = code;
+  sm.h1[lane] = h1;
+  sm.h2[lane] = h2;
+  const bool skip = (KIND == KIND_UPSERT) && (a.flags & BATCH_SKIP_SENTINELS) && is_sentinel(K);
+  const bool pre_ok = (KIND != KIND_PROBE) && tv.preload && inb && !is_sentinel(K);
+  const unsigned pre_mask = __ballot_sync(0xffffffffu, pre_ok);
+  __syncwarp();
+  if (KIND != KIND_PROBE && tv.preload) {
+    // first probe of every op, 16 bytes per lane per instruction
+    if (META) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int j = i * 8 + (lane >> 2), part = lane & 3;
+        if ((pre_mask >> j) & 1u) {
+          const u64 bj = sm.h1[j] & tv.nb_mask;
+          ptx::cp_async16(reinterpret_cast<char*>(&sm.pre[j]) + 16 * part,
+                          reinterpret_cast<const char*>(tv.tags + bj * 32) + 16 * part);
+        }
+      }
+    } else {
+      constexpr int PS = Ops::PRE_SLOTS;  // 8 slots = 128 B per op
+#pragma unroll
+      for (int i = 0; i < PS; ++i) {
+        const int j = i * (32 / PS) + lane / PS, part = lane % PS;
+        if ((pre_mask >> j) & 1u) {
+          const u64 bj = sm.h1[j] & tv.nb_mask;
+          ptx::cp_async16(&sm.pre[j].line[part], tv.slots + bj * B + (u64)part);
+        }
+      }
+    }
+    ptx::cp_async_wait_all();
+    __syncwarp();
+    if (META) {
+      if (pre_ok) Ops::preload_candidate(tv, K, &sm.pre[lane]);
+      ptx::cp_async_wait_all();
+      __syncwarp();
+    }
+  }
+
+  // lane fast path
+  int dcount = 0;
+  bool done = !inb;
+  bool fresh = true;
+  u64 out = 0;
+  u8 st = ST_MISS;
+  if (inb && skip) {
+    done = true;  // an empty / erased slot of a rehash source
+  } else if (inb && is_sentinel(K)) {
+    done = true;
+    st = ST_BADKEY;
+  } else if (pre_ok) {
+    const PreOp& p = sm.pre[lane];
+    int kind = KIND;
+    int op = upsert_op;
+    if (KIND == KIND_MIXED) {
+      kind = code == MX_QUERY ? KIND_QUERY : code == MX_ERASE ? KIND_ERASE : KIND_UPSERT;
+      op = code == MX_INSERT ? OP_INSERT : code == MX_ADD ? OP_ADD : code == MX_MAX ? OP_MAX : OP_REPLACE;
+      if (code > MX_ERASE) {
+        kind = -1;
+        done = true;
+        st = ST_BADKEY;
+      }
+    }
+    if (kind == KIND_QUERY)
+      done = Ops::lane_query(tv, p, K, b0, out, st);
+    else if (kind == KIND_ERASE)
+      done = Ops::lane_erase(tv, p, K, b0, out, st, dcount, fresh);
+    else if (kind == KIND_UPSERT)
+      done = (KIND == KIND_UPSERT && lockfree)
+                 ? Ops::template lane_upsert<true>(tv, p, K, b0, V, op, st, dcount, fresh)
+                 : Ops::template lane_upsert<false>(tv, p, K, b0, V, op, st, dcount, fresh);
+  }
+  sm.out[lane] = out;
+  sm.st[lane] = st;
+  sm.fresh[lane] = fresh ? 1 : 0;
+  if (done && inb && st >= ST_FULL) count_failure(tv, st);
+  const unsigned todo = __ballot_sync(0xffffffffu, !done);
+  __syncwarp();
+
+  // tiles take the leftovers round-robin
+  if (todo) {
+    const TileCtx<T> c = make_tile<T>(lane);
+    const int tile = lane / T;
+    constexpr int NT = 32 / T;
+    unsigned m = todo;
+    int r = 0;
+    while (m) {
+      const int j = __ffs(m) - 1;
+      m &= m - 1;
+      if ((r++ % NT) != tile) continue;
+      const u64 Kj = sm.key[j];
+      const u64 h1j = sm.h1[j], h2j = sm.h2[j];
+      const PreOp* pre = (((pre_mask >> j) & 1u) && sm.fresh[j]) ? &sm.pre[j] : nullptr;
+      u64 o = 0;
+      u8 sj;
+      if (KIND == KIND_QUERY) {
+        sj = Ops::do_query(tv, c, Kj, h1j, h2j, pre, o);
+      } else if (KIND == KIND_PROBE) {
+        sj = Ops::do_probe(tv, c, Kj, o);
+      } else if (KIND == KIND_UPSERT) {
+        sj = lockfree ? Ops::template do_upsert<true>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, pre, dcount)
+                      : Ops::template do_upsert<false>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, pre, dcount);
+      } else if (KIND == KIND_ERASE) {
+        sj = Ops::do_erase(tv, c, Kj, h1j, h2j, pre, o, dcount);
+      } else {
+        sj = Ops::do_mixed(tv, c, sm.op[j], Kj, h1j, h2j, sm.val[j], pre, o, dcount);
+      }
+      if (c.tl == 0) {
+        sm.out[j] = o;
+        sm.st[j] = sj;
+        count_failure(tv, sj);
+      }
+    }
+    // count deltas of tile work live on tile leaders only
+    if (c.tl != 0) dcount = 0;
+  }
+  __syncwarp();
+  if (inb) {
+    if (a.vals_out) a.vals_out[gi] = sm.out[lane];
+    if (a.status_out) a.status_out[gi] = sm.st[lane];
+  }
+  __syncwarp();
+  return dcount;
+}
+
 template <int SCHEME, bool META, int B, int T, int KIND>
 __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchArgs a) {
-  using Ops = TileOps<SCHEME, META, B, T>;
-  __shared__ u64 s_key[kWarps][32];
-  __shared__ u64 s_val[kWarps][32];
-  __shared__ u64 s_out[kWarps][32];
-  __shared__ u8 s_op[kWarps][32];
-  __shared__ u8 s_st[kWarps][32];
+  __shared__ WarpSmem s_w[kWarps];
   __shared__ long long s_cnt;
-
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  TileCtx<T> c;
-  c.tl = lane & (T - 1);
-  c.base = lane & ~(T - 1);
-  c.mask = (T == 32) ? 0xffffffffu : (((1u << T) - 1u) << c.base);
-  const int tile = lane / T;
   if (threadIdx.x == 0) s_cnt = 0;
   __syncthreads();
-
+  const bool lockfree = (KIND == KIND_UPSERT);  // one call is one phase: no erase runs with it
   int dcount = 0;
   const u64 nchunks = (a.n + 31) / 32;
   const u64 stride = (u64)gridDim.x * kWarps;
-  const int pf_method = (KIND == KIND_PROBE) ? 0 : (tv.prefetch & 3);
-  const bool pf_lead = (tv.prefetch & 4) != 0;
-  u64 ch = (u64)blockIdx.x * kWarps + w;
-  const u64 ks = a.key_stride ? a.key_stride : 1;
-  // keys of the chunk about to be staged (prefetched one chunk ahead with pf_lead)
-  u64 next_key = 0;
-  if (ch < nchunks) {
-    const u64 gi0 = ch * 32 + lane;
-    next_key = gi0 < a.n ? a.keys[gi0 * ks] : 0;
-    if (pf_method && gi0 < a.n) Ops::prefetch_key(tv, next_key, pf_method);
-  }
-  for (; ch < nchunks; ch += stride) {
-    const u64 base = ch * 32;
-    const u64 gi = base + lane;
-    const bool inb = gi < a.n;
-    s_key[w][lane] = next_key;
-    if (KIND == KIND_UPSERT || KIND == KIND_MIXED) s_val[w][lane] = (inb && a.vals) ? a.vals[gi * ks] : 0;
-    if (KIND == KIND_MIXED) s_op[w][lane] = inb ? a.ops[gi] : 0;
-    {
-      const u64 nch = ch + stride;
-      const u64 ngi = nch * 32 + lane;
-      next_key = (nch < nchunks && ngi < a.n) ? a.keys[ngi * ks] : 0;
-      if (pf_method && pf_lead && nch < nchunks && ngi < a.n) Ops::prefetch_key(tv, next_key, pf_method);
-    }
-    __syncwarp();
-    const int cnt = (a.n - base) < 32 ? (int)(a.n - base) : 32;
-    for (int jj = 0; jj < T; ++jj) {
-      const int j = tile * T + jj;
-      if (j >= cnt) break;
-      const u64 K = s_key[w][j];
-      u64 out = 0;
-      u8 st;
-      if (KIND == KIND_QUERY) {
-        st = Ops::do_query(tv, c, K, out);
-      } else if (KIND == KIND_PROBE) {
-        st = Ops::do_probe(tv, c, K, out);
-      } else if (KIND == KIND_UPSERT) {
-        if ((a.flags & BATCH_SKIP_SENTINELS) && is_sentinel(K))
-          st = ST_MISS;  // an empty / erased slot of the source table
-        else
-          st = Ops::template do_upsert<true>(tv, c, K, s_val[w][j], a.op, dcount);
-      } else if (KIND == KIND_ERASE) {
-        st = Ops::do_erase(tv, c, K, out, dcount);
-      } else {
-        const u8 code = s_op[w][j];
-        switch (code) {
-          case MX_QUERY: st = Ops::do_query(tv, c, K, out); break;
-          case MX_INSERT: st = Ops::template do_upsert<false>(tv, c, K, s_val[w][j], OP_INSERT, dcount); break;
-          case MX_ADD: st = Ops::template do_upsert<false>(tv, c, K, s_val[w][j], OP_ADD, dcount); break;
-          case MX_MAX: st = Ops::template do_upsert<false>(tv, c, K, s_val[w][j], OP_MAX, dcount); break;
-          case MX_REPLACE: st = Ops::template do_upsert<false>(tv, c, K, s_val[w][j], OP_REPLACE, dcount); break;
-          case MX_ERASE: st = Ops::do_erase(tv, c, K, out, dcount); break;
-          default: st = ST_BADKEY; break;
-        }
-      }
-      if (c.tl == 0) {
-        s_out[w][j] = out;
-        s_st[w][j] = st;
-        if (st >= ST_FULL) {
-          u64* ctr = st == ST_FULL ? &tv.ctr->n_full : st == ST_TIMEOUT ? &tv.ctr->n_timeout : &tv.ctr->n_badkey;
-          atomicAdd((unsigned long long*)ctr, 1ull);
-        }
-      }
-    }
-    __syncwarp();
-    if (inb) {
-      if (a.vals_out) a.vals_out[gi] = s_out[w][lane];
-      if (a.status_out) a.status_out[gi] = s_st[w][lane];
-    }
-    __syncwarp();
-  }
+  for (u64 ch = (u64)blockIdx.x * kWarps + w; ch < nchunks; ch += stride)
+    dcount += warp_chunk<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, ch * 32, s_w[w], lane);
   if (KIND != KIND_QUERY && KIND != KIND_PROBE) {
-    int mine = (c.tl == 0) ? dcount : 0;
-    mine = __reduce_add_sync(0xffffffffu, mine);
+    const int mine = __reduce_add_sync(0xffffffffu, dcount);
     if (lane == 0 && mine) atomicAdd((unsigned long long*)&s_cnt, (unsigned long long)(long long)mine);
     __syncthreads();
     if (threadIdx.x == 0 && s_cnt) atomicAdd((unsigned long long*)&tv.ctr->count, (unsigned long long)s_cnt);

@@ -41,66 +41,22 @@ struct MultiChunk {
   X(7, SCHEME_P2, true, 32, 8)
 constexpr int kMultiMenu = 8;
 
-// Serves ops [base, base + 32) of one item with one warp; returns the count
-// delta held by tile leaders (others return 0).
+// Serves ops [base, base + 32) of one item with one warp (the single-table
+// chunk routine, with the op kind chosen at run time); returns the warp's
+// count delta.
 template <int SCHEME, bool META, int B, int T>
-__device__ __forceinline__ int multi_warp(const MultiItem& it, u64 base, u64* s_key, u64* s_val, u64* s_out,
-                                          u8* s_st, int lane) {
-  using Ops = TileOps<SCHEME, META, B, T>;
-  const TableView& tv = it.tv;
-  const BatchArgs& a = it.a;
-  TileCtx<T> c;
-  c.tl = lane & (T - 1);
-  c.base = lane & ~(T - 1);
-  c.mask = (T == 32) ? 0xffffffffu : (((1u << (T & 31)) - 1u) << c.base);
-  const int tile = lane / T;
-  const u64 gi = base + lane;
-  const bool inb = gi < a.n;
-  const u64 key = inb ? a.keys[gi] : 0;
-  s_key[lane] = key;
-  if (it.kind == KIND_UPSERT) s_val[lane] = inb ? a.vals[gi] : 0;
-  if ((tv.prefetch & 3) && inb) Ops::prefetch_key(tv, key, tv.prefetch & 3);
-  __syncwarp();
-  const int cnt = (a.n - base) < 32 ? (int)(a.n - base) : 32;
-  int dcount = 0;
-  for (int jj = 0; jj < T; ++jj) {
-    const int j = tile * T + jj;
-    if (j >= cnt) break;
-    const u64 K = s_key[j];
-    u64 out = 0;
-    u8 st;
-    if (it.kind == KIND_QUERY)
-      st = Ops::do_query(tv, c, K, out);
-    else if (it.kind == KIND_UPSERT)
-      st = it.lockfree ? Ops::template do_upsert<true>(tv, c, K, s_val[j], a.op, dcount)
-                       : Ops::template do_upsert<false>(tv, c, K, s_val[j], a.op, dcount);
-    else
-      st = Ops::do_erase(tv, c, K, out, dcount);
-    if (c.tl == 0) {
-      s_out[j] = out;
-      s_st[j] = st;
-      if (st >= ST_FULL) {
-        u64* ctr = st == ST_FULL ? &tv.ctr->n_full : st == ST_TIMEOUT ? &tv.ctr->n_timeout : &tv.ctr->n_badkey;
-        atomicAdd((unsigned long long*)ctr, 1ull);
-      }
-    }
-  }
-  __syncwarp();
-  if (inb) {
-    if (a.vals_out) a.vals_out[gi] = s_out[lane];
-    if (a.status_out) a.status_out[gi] = s_st[lane];
-  }
-  __syncwarp();
-  return c.tl == 0 ? dcount : 0;
+__device__ __forceinline__ int multi_warp(const MultiItem& it, u64 base, WarpSmem& sm, int lane) {
+  if (it.kind == KIND_QUERY)
+    return warp_chunk<SCHEME, META, B, T, KIND_QUERY>(it.tv, it.a, 0, false, base, sm, lane);
+  if (it.kind == KIND_UPSERT)
+    return warp_chunk<SCHEME, META, B, T, KIND_UPSERT>(it.tv, it.a, it.a.op, it.lockfree != 0, base, sm, lane);
+  return warp_chunk<SCHEME, META, B, T, KIND_ERASE>(it.tv, it.a, 0, false, base, sm, lane);
 }
 
 __global__ void __launch_bounds__(kThreads, 2)
     multi_kernel(const MultiItem* __restrict__ items, const MultiChunk* __restrict__ chunks, u32 n_chunks,
                  u32* ticket) {
-  __shared__ u64 s_key[kWarps][32];
-  __shared__ u64 s_val[kWarps][32];
-  __shared__ u64 s_out[kWarps][32];
-  __shared__ u8 s_st[kWarps][32];
+  __shared__ WarpSmem s_w[kWarps];
   __shared__ u32 s_chunk;
   __shared__ MultiChunk s_ch;
   __shared__ __align__(16) MultiItem s_it;
@@ -130,7 +86,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       switch (it.cfg) {
 #define WS_MULTI_CASE(ID, SCH, MT, BB, TT)                                                      \
   case ID:                                                                                       \
-    d = multi_warp<SCH, MT, BB, TT>(it, base, s_key[w], s_val[w], s_out[w], s_st[w], lane); \
+    d = multi_warp<SCH, MT, BB, TT>(it, base, s_w[w], lane); \
     break;
         WS_MULTI_MENU(WS_MULTI_CASE)
 #undef WS_MULTI_CASE
@@ -138,7 +94,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       }
     }
     if (it.kind != KIND_QUERY) {
-      d = __reduce_add_sync(0xffffffffu, d);
+      d = __reduce_add_sync(0xffffffffu, d);  // every lane reaches this: base is warp-uniform
       if (lane == 0 && d) atomicAdd((unsigned long long*)&it.tv.ctr->count, (unsigned long long)(long long)d);
     }
     __syncthreads();  // s_it / s_ch are rewritten by the next iteration
