@@ -1006,7 +1006,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     }
   }
 
-  // lane fast path
+  // lane fast path (each lane counts its own op's count delta)
   int dcount = 0;
   bool done = !inb;
   bool fresh = true;
@@ -1046,7 +1046,8 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
   const unsigned todo = __ballot_sync(0xffffffffu, !done);
   __syncwarp();
 
-  // tiles take the leftovers round-robin
+  // tiles take the leftovers round-robin (a tile's delta lives on its leader)
+  int tile_d = 0;
   if (todo) {
     const TileCtx<T> c = make_tile<T>(lane);
     const int tile = lane / T;
@@ -1067,12 +1068,12 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
       } else if (KIND == KIND_PROBE) {
         sj = Ops::do_probe(tv, c, Kj, o);
       } else if (KIND == KIND_UPSERT) {
-        sj = lockfree ? Ops::template do_upsert<true>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, pre, dcount)
-                      : Ops::template do_upsert<false>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, pre, dcount);
+        sj = lockfree ? Ops::template do_upsert<true>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, pre, tile_d)
+                      : Ops::template do_upsert<false>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, pre, tile_d);
       } else if (KIND == KIND_ERASE) {
-        sj = Ops::do_erase(tv, c, Kj, h1j, h2j, pre, o, dcount);
+        sj = Ops::do_erase(tv, c, Kj, h1j, h2j, pre, o, tile_d);
       } else {
-        sj = Ops::do_mixed(tv, c, sm.op[j], Kj, h1j, h2j, sm.val[j], pre, o, dcount);
+        sj = Ops::do_mixed(tv, c, sm.op[j], Kj, h1j, h2j, sm.val[j], pre, o, tile_d);
       }
       if (c.tl == 0) {
         sm.out[j] = o;
@@ -1080,8 +1081,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
         count_failure(tv, sj);
       }
     }
-    // count deltas of tile work live on tile leaders only
-    if (c.tl != 0) dcount = 0;
+    if (c.tl != 0) tile_d = 0;
   }
   __syncwarp();
   if (inb) {
@@ -1089,7 +1089,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     if (a.status_out) a.status_out[gi] = sm.st[lane];
   }
   __syncwarp();
-  return dcount;
+  return dcount + tile_d;
 }
 
 template <int SCHEME, bool META, int B, int T, int KIND>
