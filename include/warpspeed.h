@@ -249,6 +249,22 @@ ws_status ws_batch_plan_info(const ws_batch_plan* plan, uint64_t* n_phases, uint
 /* Waits for the device, then frees the plan's device memory. */
 ws_status ws_batch_plan_destroy(ws_batch_plan* plan);
 
+/* Batched mode for callers that must not allocate device memory.  The paper
+ * has no counterpart; this is an interface for callers that cannot call
+ * cudaMalloc / cudaFree: code whose device memory is already held in full by a
+ * caching allocator, code that reserved all memory up front, and latency-
+ * critical loops that cannot take cudaFree's device-wide synchronisation.
+ * Same items and semantics as a one-phase-at-a-time ws_batch_plan, run directly
+ * (no graph), with the plan's scratch (descriptors, chunk map, work tickets)
+ * kept in one fixed device array inside the library (~170 KiB on every GPU
+ * that loads the library, held until exit) instead of allocated memory.
+ * Limits: at most 1024 items and 16 distinct phases per call; larger calls
+ * return WS_ERR_INVALID and ws_cuda_error_string() says why.  The first call
+ * on a device looks up the array's device address (make that call before any
+ * stream capture).  Every call reuses the array: calls whose work overlaps on
+ * the GPU race, so order them on one stream.  Device pointers only. */
+ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n_items, ws_stream stream);
+
 /* Text of the last CUDA error seen by this library on the calling thread. */
 const char* ws_cuda_error_string(void);
 const char* ws_status_string(ws_status s);

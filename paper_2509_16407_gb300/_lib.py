@@ -68,6 +68,7 @@ SIGNATURES = {
     "ws_batch_plan_info": (st, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                 ctypes.POINTER(ctypes.c_uint64)]),
     "ws_batch_plan_destroy": (st, [vp]),
+    "ws_batch_run_noalloc": (st, [ctypes.POINTER(WsBatchItem), u64, vp]),
     "ws_cuda_error_string": (ctypes.c_char_p, []),
     "ws_status_string": (ctypes.c_char_p, [i32]),
     "ws_version": (u32, []),

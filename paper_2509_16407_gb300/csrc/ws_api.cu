@@ -15,6 +15,8 @@ void note_cuda(cudaError_t e, const char* where) {
   std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
 }
 
+void note_text(const char* msg) { std::snprintf(g_cuda_err, sizeof(g_cuda_err), "%s", msg); }
+
 }  // namespace wsi
 
 using namespace wsi;

@@ -27,6 +27,8 @@ struct Staging {
 };
 
 void note_cuda(cudaError_t e, const char* where);
+// Replace the thread's error text (read back by ws_cuda_error_string).
+void note_text(const char* msg);
 
 struct DeviceGuard {
   int prev = -1;

@@ -53,6 +53,7 @@ __device__ __forceinline__ int multi_warp(const MultiItem& it, u64 base, WarpSme
   return warp_chunk<SCHEME, META, B, T, KIND_ERASE>(it.tv, it.a, 0, false, base, sm, lane);
 }
 
+#ifndef WS_MULTI_NO_KERNEL  // units that only need the pieces above define this
 __global__ void __launch_bounds__(kThreads, 2)
     multi_kernel(const MultiItem* __restrict__ items, const MultiChunk* __restrict__ chunks, u32 n_chunks,
                  u32* ticket) {
@@ -100,6 +101,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();  // s_it / s_ch are rewritten by the next iteration
   }
 }
+#endif
 
 // Menu index of a configuration, or -1.
 inline int multi_menu_index(int scheme, bool meta, int B, int T) {

@@ -1,0 +1,268 @@
+// ws_noalloc.cu -- ws_batch_run_noalloc: batched mode without any device
+// allocation.
+//
+// Who needs it: code that must not call cudaMalloc / cudaFree -- a caller
+// running inside a memory budget that a caching allocator (a framework's
+// pool) already holds in full, a latency-critical loop that cannot afford
+// cudaFree's implicit device-wide synchronisation, or a process that has
+// reserved all device memory up front.  ws_batch_plan_create allocates its
+// descriptor, chunk and ticket arrays; this entry point keeps the same
+// scratch in one fixed, file-scope device array instead, so a call
+// allocates nothing.
+//
+// The array (kScratchBytes, about 170 KiB) exists on every GPU that loads
+// the library until the process exits.  Its device address is looked up once
+// per device, on the first call that uses that device (cudaGetSymbolAddress
+// with the device current); make that first call before any stream capture.
+// Every call reuses the same array and it keeps the last call's contents:
+// each call rewrites the descriptors it uses and zeroes its work tickets.
+// Calls whose work overlaps on the GPU race on the array -- order them on one
+// stream or synchronise between them.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "ws_internal.h"
+#define WS_MULTI_NO_KERNEL
+#include "ws_multi.cuh"
+
+using namespace wsi;
+
+namespace {
+
+constexpr uint32_t kMaxItems = 1024;  // items per call
+constexpr uint32_t kMaxPhases = 16;   // distinct phases per call
+constexpr int kMaxDevices = 64;
+
+// Layout of the scratch array.
+struct NoallocScratch {
+  u32 tickets[kMaxPhases];        // one work ticket per phase, zeroed by every call
+  u32 prefix[kMaxItems + 1];      // chunk prefix sums over the (phase-sorted) items
+  u32 pad[(256 - ((kMaxPhases + kMaxItems + 1) * 4) % 256) / 4];
+  ws::MultiItem items[kMaxItems];
+};
+constexpr size_t kScratchBytes = sizeof(NoallocScratch);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+std::mutex g_mu;
+NoallocScratch* g_scratch_of[kMaxDevices] = {};
+
+// Device address of the scratch array on `dev` (current device), looked up once.
+cudaError_t scratch_for(int dev, NoallocScratch** out) {
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  if (!g_scratch_of[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_of[dev] = static_cast<NoallocScratch*>(p);
+  }
+  *out = g_scratch_of[dev];
+  return cudaSuccess;
+}
+
+// The persistent multi-table kernel, reading its chunk map from the prefix
+// sums of the scratch array: chunk g belongs to the item i with
+// prefix[i] <= g < prefix[i + 1].  Items [i0, i1) form one phase.
+__global__ void __launch_bounds__(ws::kThreads, 2)
+    multi_kernel_prefix(const ws::MultiItem* __restrict__ items, const u32* __restrict__ prefix, u32 i0, u32 i1,
+                        u32* ticket) {
+  __shared__ ws::WarpSmem s_w[ws::kWarps];
+  __shared__ u32 s_item;
+  __shared__ u64 s_start;
+  __shared__ int s_stop;
+  __shared__ __align__(16) ws::MultiItem s_it;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const u32 first = prefix[i0], count = prefix[i1] - prefix[i0];
+  u32 cur_item = 0xffffffffu;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const u32 c = atomicAdd(ticket, 1u);
+      s_stop = c >= count;
+      if (!s_stop) {
+        const u32 g = first + c;
+        u32 lo = i0, hi = i1 - 1;  // largest i with prefix[i] <= g
+        while (lo < hi) {
+          const u32 mid = (lo + hi + 1) / 2;
+          if (prefix[mid] <= g)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        s_item = lo;
+        s_start = (u64)(g - prefix[lo]) * ws::kMultiChunk;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const u32 item = s_item;
+    const u64 start = s_start;
+    if (item != cur_item) {
+      const u64* src = reinterpret_cast<const u64*>(items + item);
+      u64* dst = reinterpret_cast<u64*>(&s_it);
+      for (int q = threadIdx.x; q < (int)(sizeof(ws::MultiItem) / 8); q += blockDim.x) dst[q] = src[q];
+      cur_item = item;
+    }
+    __syncthreads();
+    const ws::MultiItem& it = s_it;
+    const u64 base = start + (u64)w * 32;
+    int d = 0;
+    if (base < it.a.n) {
+      switch (it.cfg) {
+#define WS_NOALLOC_CASE(ID, SCH, MT, BB, TT)                   \
+  case ID:                                                     \
+    d = ws::multi_warp<ws::SCH, MT, BB, TT>(it, base, s_w[w], lane); \
+    break;
+        WS_MULTI_MENU(WS_NOALLOC_CASE)
+#undef WS_NOALLOC_CASE
+        default: break;
+      }
+    }
+    if (it.kind != ws::KIND_QUERY) {
+      d = __reduce_add_sync(0xffffffffu, d);
+      if (lane == 0 && d) atomicAdd((unsigned long long*)&it.tv.ctr->count, (unsigned long long)(long long)d);
+    }
+    __syncthreads();
+  }
+}
+
+int kind_of(int bk) {
+  return bk == WS_BK_QUERY ? ws::KIND_QUERY : bk == WS_BK_ERASE ? ws::KIND_ERASE : ws::KIND_UPSERT;
+}
+
+// Host-side staging of one call's descriptors (per thread, no heap).
+struct HostStage {
+  uint32_t order[kMaxItems];
+  ws::MultiItem items[kMaxItems];
+  u32 prefix[kMaxItems + 1];
+  u32 phase_begin[kMaxPhases + 1];
+  int phase_value[kMaxPhases];
+};
+thread_local HostStage t_stage;
+
+}  // namespace
+
+extern "C" ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n_items, ws_stream stream) {
+  if (n_items == 0) return WS_OK;
+  if (!items) return WS_ERR_INVALID;
+  if (n_items > kMaxItems) {
+    char msg[128];
+    std::snprintf(msg, sizeof(msg), "ws_batch_run_noalloc: %llu items exceed the maximum of %u per call",
+                  (unsigned long long)n_items, kMaxItems);
+    note_text(msg);
+    return WS_ERR_INVALID;
+  }
+  const int dev = items[0].table ? items[0].table->device : -1;
+  for (uint64_t i = 0; i < n_items; ++i) {
+    const ws_batch_item& it = items[i];
+    if (!it.table || it.table->device != dev) return WS_ERR_INVALID;
+    if (it.kind < WS_BK_INSERT || it.kind > WS_BK_ERASE || it.phase < 0) return WS_ERR_INVALID;
+    if (it.kind == WS_BK_UPSERT && (it.op < WS_OP_ADD || it.op > WS_OP_INSERT)) return WS_ERR_INVALID;
+    if (it.n == 0) continue;
+    if (!it.keys || ((reinterpret_cast<uintptr_t>(it.keys) | reinterpret_cast<uintptr_t>(it.vals) |
+                      reinterpret_cast<uintptr_t>(it.vals_out)) & 7u))
+      return WS_ERR_INVALID;
+    if ((it.kind == WS_BK_INSERT || it.kind == WS_BK_UPSERT) && !it.vals) return WS_ERR_INVALID;
+    if (it.kind == WS_BK_QUERY && !it.vals_out && !it.status_out) return WS_ERR_INVALID;
+  }
+  DeviceGuard guard(dev);
+  for (uint64_t i = 0; i < n_items; ++i) {
+    const ws_batch_item& it = items[i];
+    if (it.n == 0) continue;
+    const void* ptrs[4] = {it.keys, it.vals, it.vals_out, it.status_out};
+    for (const void* q : ptrs)
+      if (q && classify(q, dev) != PTR_DEVICE) return WS_ERR_INVALID;  // device-resident only
+  }
+  NoallocScratch* scratch = nullptr;
+  WS_CUDA(scratch_for(dev, &scratch));
+  int num_sms = 0;
+  WS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+
+  HostStage& hs = t_stage;
+  // stable order by phase (insertion sort: at most kMaxItems, no allocation)
+  for (uint32_t i = 0; i < (uint32_t)n_items; ++i) {
+    uint32_t k = i;
+    while (k > 0 && items[hs.order[k - 1]].phase > items[i].phase) {
+      hs.order[k] = hs.order[k - 1];
+      --k;
+    }
+    hs.order[k] = i;
+  }
+  // phases; tables erased anywhere in the call lose the two-choice shortcut
+  // for the whole call, and a table erased in a phase takes the locked
+  // insert path in that phase
+  uint32_t n_ph = 0;
+  for (uint32_t k = 0; k < (uint32_t)n_items; ++k) {
+    const int ph = items[hs.order[k]].phase;
+    if (n_ph == 0 || hs.phase_value[n_ph - 1] != ph) {
+      if (n_ph == kMaxPhases) {
+        char msg[128];
+        std::snprintf(msg, sizeof(msg), "ws_batch_run_noalloc: more than %u distinct phases in one call", kMaxPhases);
+        note_text(msg);
+        return WS_ERR_INVALID;
+      }
+      hs.phase_value[n_ph] = ph;
+      hs.phase_begin[n_ph] = k;
+      ++n_ph;
+    }
+  }
+  hs.phase_begin[n_ph] = (uint32_t)n_items;
+  hs.prefix[0] = 0;
+  uint64_t chunks = 0;
+  for (uint32_t k = 0; k < (uint32_t)n_items; ++k) {
+    const ws_batch_item& s = items[hs.order[k]];
+    const ws_table* t = s.table;
+    bool erased_call = false, erased_phase = false;
+    for (uint64_t q = 0; q < n_items; ++q) {
+      if (items[q].table != t || items[q].kind != WS_BK_ERASE) continue;
+      erased_call = true;
+      if (items[q].phase == s.phase) erased_phase = true;
+    }
+    ws::MultiItem& m = hs.items[k];
+    std::memset(&m, 0, sizeof(m));
+    m.tv = t->tv;
+    m.tv.shortcut = (t->never_erased && !erased_call) ? 1 : 0;
+    m.a.keys = reinterpret_cast<const u64*>(s.keys);
+    m.a.vals = reinterpret_cast<const u64*>(s.vals);
+    m.a.vals_out = reinterpret_cast<u64*>(s.vals_out);
+    m.a.status_out = s.status_out;
+    m.a.n = s.n;
+    m.a.op = s.kind == WS_BK_INSERT ? ws::OP_INSERT : s.op;
+    m.a.key_stride = 1;
+    m.kind = kind_of(s.kind);
+    m.cfg = ws::multi_menu_index(t->scheme, t->meta != 0, (int)t->B, t->T);
+    m.lockfree = (m.kind == ws::KIND_UPSERT && !erased_phase) ? 1 : 0;
+    // items outside the compiled menu run as single-table kernels below
+    const u64 nc = (m.cfg >= 0) ? (s.n + ws::kMultiChunk - 1) / ws::kMultiChunk : 0;
+    chunks += nc;
+    if (chunks > 0xffffffffull) return WS_ERR_INVALID;
+    hs.prefix[k + 1] = (u32)chunks;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  WS_CUDA(cudaMemcpyAsync(scratch->prefix, hs.prefix, (n_items + 1) * sizeof(u32), cudaMemcpyHostToDevice, st));
+  WS_CUDA(cudaMemcpyAsync(scratch->items, hs.items, n_items * sizeof(ws::MultiItem), cudaMemcpyHostToDevice, st));
+  WS_CUDA(cudaMemsetAsync(scratch->tickets, 0, sizeof(scratch->tickets), st));
+  int occ = 0;
+  WS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, multi_kernel_prefix, ws::kThreads, 0));
+  const u64 grid_cap = (u64)(occ > 0 ? occ : 1) * (u64)num_sms;
+  for (uint32_t p = 0; p < n_ph; ++p) {
+    const uint32_t i0 = hs.phase_begin[p], i1 = hs.phase_begin[p + 1];
+    const u64 nch = hs.prefix[i1] - hs.prefix[i0];
+    if (nch) {
+      const unsigned g = (unsigned)(nch < grid_cap ? nch : grid_cap);
+      multi_kernel_prefix<<<g, ws::kThreads, 0, st>>>(scratch->items, scratch->prefix, i0, i1, scratch->tickets + p);
+      WS_CUDA(cudaGetLastError());
+    }
+    for (uint32_t k = i0; k < i1; ++k) {  // configurations outside the menu
+      const ws::MultiItem& m = hs.items[k];
+      if (m.cfg >= 0 || m.a.n == 0) continue;
+      WS_CUDA(dispatch(items[hs.order[k]].table, m.tv, m.a, m.kind, st));
+    }
+  }
+  for (uint64_t i = 0; i < n_items; ++i) {
+    items[i].table->last_stream = st;
+    if (items[i].kind == WS_BK_ERASE) items[i].table->never_erased = 0;
+  }
+  return WS_OK;
+}
