@@ -79,14 +79,28 @@ __device__ __forceinline__ TileCtx<T> make_tile(int lane) {
   return c;
 }
 
-// First-probe snapshot of one op (128 B, in shared memory).  Plain tables:
-// the first 8 slots of b_0.  Metadata tables: the 32 tags of b_0 in bytes
-// 0..63, the first tag-matching slot's pair in line[4], its slot index in
-// line[5].key (~0 when no tag matched).
-struct __align__(16) PreOp {
-  Slot line[8];
+// First-probe snapshots of a warp's 32 ops, in shared memory, stored
+// slot-major with one spare column: a lane reading its own op's slots and a
+// tile reading one op's slots both hit distinct banks.  Plain tables: row s =
+// slot s of b_0 (s < 8).  Metadata tables: rows 0..3 = the 32 tags of b_0
+// (eight per row), row 4 = the first tag-matching slot's pair, row 5 .key =
+// that slot's index (~0 when no tag matched).
+struct __align__(16) PreWarp {
+  Slot line[8][33];
 };
 constexpr u64 kNoCand = ~0ull;
+
+// One op's view of its warp's snapshots (w == nullptr: no snapshot).
+struct PreRef {
+  const PreWarp* w;
+  int j;
+  __device__ __forceinline__ bool ok() const { return w != nullptr; }
+  __device__ __forceinline__ Slot slot(int s) const { return w->line[s][j]; }
+  __device__ __forceinline__ const u16* tagrow(int r) const { return reinterpret_cast<const u16*>(&w->line[r][j]); }
+  __device__ __forceinline__ Slot cand() const { return w->line[4][j]; }
+  __device__ __forceinline__ u64 cand_idx() const { return w->line[5][j].key; }
+};
+__device__ __forceinline__ PreRef no_pre() { return PreRef{nullptr, 0}; }
 
 template <int SCHEME, bool META, int B, int T>
 struct TileOps {
@@ -129,36 +143,23 @@ struct TileOps {
   // ----------------------------------------------------------------------
   // First-probe preload (one lane per op; see the file comment)
   // ----------------------------------------------------------------------
-  __device__ static __forceinline__ void preload_issue(const TableView& tv, u64 K, PreOp* p) {
-    const u64 b0 = fmix64(K ^ tv.seed1) & tv.nb_mask;
-    if (META) {
-      const char* src = reinterpret_cast<const char*>(tv.tags + b0 * 32);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) ptx::cp_async16(reinterpret_cast<char*>(p) + 16 * i, src + 16 * i);
-    } else {
-      const Slot* src = tv.slots + b0 * B;
-#pragma unroll
-      for (int i = 0; i < PRE_SLOTS; ++i) ptx::cp_async16(&p->line[i], src + i);
-    }
-  }
-  // Metadata second wave: the first slot of b_0 whose tag matches K.
-  __device__ static __forceinline__ void preload_candidate(const TableView& tv, u64 K, PreOp* p) {
+  // Metadata second wave: the first slot of b_0 whose tag matches K, for op j.
+  __device__ static __forceinline__ void preload_candidate(const TableView& tv, u64 K, PreWarp* pw, int j) {
     const u64 b0 = fmix64(K ^ tv.seed1) & tv.nb_mask;
     const u16 kt = key_tag(K);
-    const u64* w = reinterpret_cast<const u64*>(p);
     int q = -1;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const u64 x = w[i];
+    for (int r = 0; r < 4; ++r) {
+      const u16* t = reinterpret_cast<const u16*>(&pw->line[r][j]);
 #pragma unroll
-      for (int h = 0; h < 4; ++h)
-        if (q < 0 && (u16)((x >> (16 * h)) & 0xffffu) == kt) q = 4 * i + h;
+      for (int h = 0; h < 8; ++h)
+        if (q < 0 && t[h] == kt) q = 8 * r + h;
     }
     if (q >= 0) {
-      ptx::cp_async16(&p->line[4], tv.slots + b0 * 32 + (u64)q);
-      p->line[5].key = b0 * 32 + (u64)q;
+      ptx::cp_async16(&pw->line[4][j], tv.slots + b0 * 32 + (u64)q);
+      pw->line[5][j].key = b0 * 32 + (u64)q;
     } else {
-      p->line[5].key = kNoCand;
+      pw->line[5][j].key = kNoCand;
     }
   }
 
@@ -171,13 +172,13 @@ struct TileOps {
   static constexpr u32 kStepLines = (LPB * 16 + 127) / 128;
 
   // Slot read of a probe step: from the snapshot when it holds the slot.
-  __device__ static __forceinline__ void step_read(const TableView& tv, const PreOp* pre, bool first, int g,
+  __device__ static __forceinline__ void step_read(const TableView& tv, PreRef pre, bool first, int g,
                                                    int sl, u64 si, bool act, u64& k, u64& v) {
     k = KEY_RESV;
     v = 0;
     if (!act) return;
-    if (pre && first && g == 0 && sl < PRE_SLOTS) {
-      const Slot s = pre->line[sl];
+    if (pre.ok() && first && g == 0 && sl < PRE_SLOTS) {
+      const Slot s = pre.slot(sl);
       k = s.key;
       v = s.val;
     } else {
@@ -187,7 +188,7 @@ struct TileOps {
 
   template <bool COUNT = false>
   __device__ static Hit find_plain(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
-                                   const PreOp* pre = nullptr, u32* sectors = nullptr, u32* lines = nullptr) {
+                                   PreRef pre = PreRef{nullptr, 0}, u32* sectors = nullptr, u32* lines = nullptr) {
     const u32 P = nprobe(tv);
     const int g = c.tl / LPB, j = c.tl % LPB;
     u32 occ0 = 0;
@@ -227,7 +228,7 @@ struct TileOps {
   }
 
   __device__ static Scan scan_plain(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
-                                    const PreOp* pre) {
+                                    PreRef pre) {
     Scan r;
     r.stuck = false;
     r.found = false;
@@ -353,14 +354,16 @@ struct TileOps {
   // Metadata buckets: 32 slots, 64-byte tag line, TPL tags per lane
   // ----------------------------------------------------------------------
   __device__ static __forceinline__ void tag_masks(const TableView& tv, const TileCtx<T>& c, u64 b, u16 kt,
-                                                   const PreOp* pre, unsigned& mm, unsigned& me,
+                                                   PreRef pre, unsigned& mm, unsigned& me,
                                                    unsigned& mf) {
-    const u16* tp = pre ? reinterpret_cast<const u16*>(pre) + c.tl * TPL : tv.tags + b * 32 + (u64)(c.tl * TPL);
+    const u16* tp = tv.tags + b * 32 + (u64)(c.tl * TPL);
     unsigned lm = 0, le = 0, lf = 0;
     u16 t[TPL];
-    if (pre) {
+    if (pre.ok()) {
+      const int q0 = c.tl * TPL;  // TPL tags inside one row of eight
+      const u16* sp = pre.tagrow(q0 >> 3) + (q0 & 7);
 #pragma unroll
-      for (int q = 0; q < TPL; ++q) t[q] = tp[q];
+      for (int q = 0; q < TPL; ++q) t[q] = sp[q];
     } else if (TPL == 8) {
       u64 a0, a1;
       ptx::ld_tags16(tp, a0, a1);
@@ -411,15 +414,15 @@ struct TileOps {
   // *stuck reports a wait that ran out.
   template <bool WAIT = false, bool COUNT = false>
   __device__ static __forceinline__ bool verify(const TableView& tv, const TileCtx<T>& c, u64 b, unsigned mm,
-                                                u64 K, const PreOp* pre, u64& idx, u64& val,
+                                                u64 K, PreRef pre, u64& idx, u64& val,
                                                 bool* stuck = nullptr, u32* nread = nullptr) {
     while (mm) {
       const int q = __ffs(mm) - 1;
       mm &= mm - 1;
       const u64 si = b * 32 + (u64)q;
       u64 k, v;
-      if (pre && pre->line[5].key == si) {
-        const Slot s = pre->line[4];
+      if (pre.ok() && pre.cand_idx() == si) {
+        const Slot s = pre.cand();
         k = s.key;
         v = s.val;
       } else {
@@ -449,12 +452,12 @@ struct TileOps {
   // each candidate slot read is one 32-byte sector of one line.
   template <bool COUNT = false>
   __device__ static Hit find_meta(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
-                                  const PreOp* pre = nullptr, u32* sectors = nullptr, u32* lines = nullptr) {
+                                  PreRef pre = PreRef{nullptr, 0}, u32* sectors = nullptr, u32* lines = nullptr) {
     const u32 P = nprobe(tv);
     const u16 kt = key_tag(K);
     for (u32 i = 0; i < P; ++i) {
       const u64 b = bucket(tv, h1, h2, i);
-      const PreOp* p = (i == 0) ? pre : nullptr;
+      const PreRef p = (i == 0) ? pre : no_pre();
       unsigned mm, me, mf;
       tag_masks(tv, c, b, kt, p, mm, me, mf);
       u64 idx, val;
@@ -476,7 +479,7 @@ struct TileOps {
 
   template <bool WAIT = false>
   __device__ static Scan scan_meta(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
-                                   const PreOp* pre) {
+                                   PreRef pre) {
     Scan r;
     r.stuck = false;
     r.found = false;
@@ -487,7 +490,7 @@ struct TileOps {
     if (SCHEME == SCHEME_DOUBLE) {
       for (u32 i = 0; i < P; ++i) {
         const u64 b = bucket(tv, h1, h2, i);
-        const PreOp* p = (i == 0) ? pre : nullptr;
+        const PreRef p = (i == 0) ? pre : no_pre();
         unsigned mm, me, mf;
         tag_masks(tv, c, b, kt, p, mm, me, mf);
         if (verify<WAIT>(tv, c, b, mm, K, p, r.idx, r.val, &r.stuck)) {
@@ -511,7 +514,7 @@ struct TileOps {
     bool decided0 = (P == 1);
     for (u32 bi = 0; bi < P; ++bi) {
       const u64 b = bucket(tv, h1, h2, bi);
-      const PreOp* p = (bi == 0) ? pre : nullptr;
+      const PreRef p = (bi == 0) ? pre : no_pre();
       unsigned mm, me, mf;
       tag_masks(tv, c, b, kt, p, mm, me, mf);
       if (verify<WAIT>(tv, c, b, mm, K, p, r.idx, r.val, &r.stuck)) {
@@ -548,13 +551,13 @@ struct TileOps {
   // Shared pieces
   // ----------------------------------------------------------------------
   __device__ static __forceinline__ Hit find(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
-                                             const PreOp* pre) {
+                                             PreRef pre) {
     if (META) return find_meta(tv, c, K, h1, h2, pre);
     return find_plain(tv, c, K, h1, h2, pre);
   }
   template <bool WAIT = false>
   __device__ static __forceinline__ Scan scan(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
-                                              const PreOp* pre) {
+                                              PreRef pre) {
     if (META) return scan_meta<WAIT>(tv, c, K, h1, h2, pre);
     return scan_plain(tv, c, K, h1, h2, pre);
   }
@@ -620,7 +623,7 @@ struct TileOps {
   // Operations (tile-uniform control flow; results valid on every lane).
   // pre: the op's first-probe snapshot, or null.
   // ----------------------------------------------------------------------
-  __device__ static u8 do_query(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, const PreOp* pre,
+  __device__ static u8 do_query(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, PreRef pre,
                                 u64& out) {
     out = 0;
     if (is_sentinel(K)) return ST_BADKEY;
@@ -639,9 +642,9 @@ struct TileOps {
     u32 sec = 0, lin = 0;
     Hit h;
     if (META)
-      h = find_meta<true>(tv, c, K, h1, h2, nullptr, &sec, &lin);
+      h = find_meta<true>(tv, c, K, h1, h2, no_pre(), &sec, &lin);
     else
-      h = find_plain<true>(tv, c, K, h1, h2, nullptr, &sec, &lin);
+      h = find_plain<true>(tv, c, K, h1, h2, no_pre(), &sec, &lin);
     out = ((u64)lin << 32) | (u64)sec;
     return h.found ? ST_FOUND : ST_MISS;
   }
@@ -650,7 +653,7 @@ struct TileOps {
   // plain insert / upsert call is one phase).
   template <bool LOCKFREE>
   __device__ static u8 do_upsert(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, u64 V, int op,
-                                 const PreOp* pre, int& dcount) {
+                                 PreRef pre, int& dcount) {
     if (is_sentinel(K)) return ST_BADKEY;
     if (LOCKFREE && SCHEME == SCHEME_DOUBLE) {
       // Without erases, free slots only disappear, so every inserter of K
@@ -662,14 +665,14 @@ struct TileOps {
       // first scan may use the snapshot: a stale free slot only makes the
       // CAS fail, and the rescans read afresh.
       for (int attempt = 0; attempt < 256; ++attempt) {
-        const Scan r = scan<true>(tv, c, K, h1, h2, attempt == 0 ? pre : nullptr);
+        const Scan r = scan<true>(tv, c, K, h1, h2, attempt == 0 ? pre : no_pre());
         if (r.stuck) return ST_TIMEOUT;
         if (r.found) {
           if (c.tl == 0) apply(tv, r.idx, op, V);
           return ST_FOUND;
         }
         if (!r.has_free) {
-          if (attempt == 0 && pre) continue;  // confirm a full sequence on fresh data
+          if (attempt == 0 && pre.ok()) continue;  // confirm a full sequence on fresh data
           return ST_FULL;
         }
         if (claim(tv, c, r, K, V)) {
@@ -692,7 +695,7 @@ struct TileOps {
     const u64 b0 = bucket(tv, h1, h2, 0);
     for (u32 tries = 0, ns = 0;;) {
       if (try_lock(tv, c, b0)) break;
-      const Hit again = find(tv, c, K, h1, h2, nullptr);
+      const Hit again = find(tv, c, K, h1, h2, no_pre());
       if (again.found) {
         if (c.tl == 0) apply(tv, again.idx, op, V);
         return ST_FOUND;
@@ -702,7 +705,7 @@ struct TileOps {
     }
     u8 st = ST_TIMEOUT;
     for (int attempt = 0; attempt < 256; ++attempt) {
-      const Scan r = scan(tv, c, K, h1, h2, nullptr);
+      const Scan r = scan(tv, c, K, h1, h2, no_pre());
       if (r.found) {
         if (c.tl == 0) apply(tv, r.idx, op, V);
         st = ST_FOUND;
@@ -722,12 +725,12 @@ struct TileOps {
     return st;
   }
 
-  __device__ static u8 do_erase(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, const PreOp* pre,
+  __device__ static u8 do_erase(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, PreRef pre,
                                 u64& out, int& dcount) {
     out = 0;
     if (is_sentinel(K)) return ST_BADKEY;
     for (int attempt = 0; attempt < 256; ++attempt) {
-      const Hit h = find(tv, c, K, h1, h2, attempt == 0 ? pre : nullptr);
+      const Hit h = find(tv, c, K, h1, h2, attempt == 0 ? pre : no_pre());
       if (!h.found) return ST_MISS;
       int ok = 0;
       if (c.tl == 0) {
@@ -745,7 +748,7 @@ struct TileOps {
 
   // One op of the mixed codes (queries, upserts under the locked path, erases).
   __device__ static __forceinline__ u8 do_mixed(const TableView& tv, const TileCtx<T>& c, u8 code, u64 K, u64 h1,
-                                                u64 h2, u64 V, const PreOp* pre, u64& out, int& dcount) {
+                                                u64 h2, u64 V, PreRef pre, u64& out, int& dcount) {
     out = 0;
     switch (code) {
       case MX_QUERY: return do_query(tv, c, K, h1, h2, pre, out);
@@ -774,7 +777,7 @@ struct TileOps {
     bool unsure;     // metadata: a tag match that the snapshot cannot settle
   };
 
-  __device__ static __forceinline__ Snap snap_of(const PreOp& p, u64 K) {
+  __device__ static __forceinline__ Snap snap_of(PreRef p, u64 K) {
     Snap sn;
     sn.hit = -1;
     sn.ffree = -1;
@@ -785,7 +788,7 @@ struct TileOps {
     if (!META) {
 #pragma unroll
       for (int s = 0; s < PRE_SLOTS; ++s) {
-        const u64 k = p.line[s].key;
+        const u64 k = p.slot(s).key;
         if (k == K && sn.hit < 0) sn.hit = s;
         const bool fr = (k == KEY_EMPTY || k == KEY_TOMB);
         if (fr && sn.ffree < 0) {
@@ -797,11 +800,10 @@ struct TileOps {
       }
     } else {
       const u16 kt = key_tag(K);
-      const u64* w = reinterpret_cast<const u64*>(&p);
       int nmatch = 0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const u64 x = w[i];
+      for (int i = 0; i < 8; ++i) {  // eight words of four tags, two per row
+        const u64 x = reinterpret_cast<const u64*>(p.tagrow(i >> 1))[i & 1];
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
           const u16 t = (u16)((x >> (16 * h)) & 0xffffu);
@@ -816,7 +818,7 @@ struct TileOps {
         }
       }
       if (nmatch > 0) {
-        const u64 ck = p.line[4].key;
+        const u64 ck = p.cand().key;
         if (ck == K)
           sn.hit = 0;  // the candidate pair is K's
         else if (nmatch > 1 || ck == KEY_EMPTY || ck == KEY_TOMB)
@@ -827,13 +829,13 @@ struct TileOps {
   }
 
   // Slot index and pair of the snapshot hit.
-  __device__ static __forceinline__ void hit_pair(const PreOp& p, const Snap& sn, u64 b0, u64& idx, u64& val) {
+  __device__ static __forceinline__ void hit_pair(PreRef p, const Snap& sn, u64 b0, u64& idx, u64& val) {
     if (META) {
-      idx = p.line[5].key;
-      val = p.line[4].val;
+      idx = p.cand_idx();
+      val = p.cand().val;
     } else {
       idx = b0 * B + (u64)sn.hit;
-      val = p.line[sn.hit].val;
+      val = p.slot(sn.hit).val;
     }
   }
 
@@ -844,7 +846,7 @@ struct TileOps {
     return tv.shortcut && sn.occ < FILL_SHORTCUT && tv.nb_mask != 0;
   }
 
-  __device__ static __forceinline__ bool lane_query(const TableView& tv, const PreOp& p, u64 K, u64 b0, u64& out,
+  __device__ static __forceinline__ bool lane_query(const TableView& tv, PreRef p, u64 K, u64 b0, u64& out,
                                                     u8& st) {
     const Snap sn = snap_of(p, K);
     if (sn.hit >= 0) {
@@ -866,7 +868,7 @@ struct TileOps {
   // slot that ended the existence scan, so it is the first free slot of the
   // probe sequence).
   template <bool LOCKFREE>
-  __device__ static __forceinline__ bool lane_upsert(const TableView& tv, const PreOp& p, u64 K, u64 b0, u64 V, int op,
+  __device__ static __forceinline__ bool lane_upsert(const TableView& tv, PreRef p, u64 K, u64 b0, u64 V, int op,
                                                      u8& st, int& dcount, bool& fresh) {
     const Snap sn = snap_of(p, K);
     if (sn.hit >= 0) {
@@ -884,7 +886,7 @@ struct TileOps {
       ok = ptx::cas_tag(tv.tags + fi, expect, key_tag(K)) == expect;
       if (ok) ptx::st_slot_release(tv.slots + fi, K, V);
     } else {
-      const Slot o = p.line[sn.ffree];
+      const Slot o = p.slot(sn.ffree);
       ok = ptx::cas_slot(tv.slots + fi, o.key, o.val, K, V);
     }
     if (!ok) {
@@ -896,7 +898,7 @@ struct TileOps {
     return true;
   }
 
-  __device__ static __forceinline__ bool lane_erase(const TableView& tv, const PreOp& p, u64 K, u64 b0, u64& out,
+  __device__ static __forceinline__ bool lane_erase(const TableView& tv, PreRef p, u64 K, u64 b0, u64& out,
                                                     u8& st, int& dcount, bool& fresh) {
     const Snap sn = snap_of(p, K);
     if (sn.hit >= 0) {
@@ -948,7 +950,7 @@ constexpr int kWarps = kThreads / 32;
 struct WarpSmem {
   u64 key[32], val[32], out[32], h1[32], h2[32];
   u8 op[32], st[32], fresh[32], pad[32];
-  PreOp pre[32];
+  PreWarp pre;
 };
 
 enum { FLAG_SNAP = 1, FLAG_DONE = 2 };
@@ -982,8 +984,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
         const int j = i * 8 + (lane >> 2), part = lane & 3;
         if ((pre_mask >> j) & 1u) {
           const u64 bj = sm.h1[j] & tv.nb_mask;
-          ptx::cp_async16(reinterpret_cast<char*>(&sm.pre[j]) + 16 * part,
-                          reinterpret_cast<const char*>(tv.tags + bj * 32) + 16 * part);
+          ptx::cp_async16(&sm.pre.line[part][j], tv.tags + bj * 32 + 8 * part);
         }
       }
     } else {
@@ -993,14 +994,14 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
         const int j = i * (32 / PS) + lane / PS, part = lane % PS;
         if ((pre_mask >> j) & 1u) {
           const u64 bj = sm.h1[j] & tv.nb_mask;
-          ptx::cp_async16(&sm.pre[j].line[part], tv.slots + bj * B + (u64)part);
+          ptx::cp_async16(&sm.pre.line[part][j], tv.slots + bj * B + (u64)part);
         }
       }
     }
     ptx::cp_async_wait_all();
     __syncwarp();
     if (META) {
-      if (pre_ok) Ops::preload_candidate(tv, K, &sm.pre[lane]);
+      if (pre_ok) Ops::preload_candidate(tv, K, &sm.pre, lane);
       ptx::cp_async_wait_all();
       __syncwarp();
     }
@@ -1018,7 +1019,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     done = true;
     st = ST_BADKEY;
   } else if (pre_ok) {
-    const PreOp& p = sm.pre[lane];
+    const PreRef p{&sm.pre, lane};
     int kind = KIND;
     int op = upsert_op;
     if (KIND == KIND_MIXED) {
@@ -1052,15 +1053,16 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     const TileCtx<T> c = make_tile<T>(lane);
     const int tile = lane / T;
     constexpr int NT = 32 / T;
-    unsigned m = todo;
-    int r = 0;
-    while (m) {
-      const int j = __ffs(m) - 1;
-      m &= m - 1;
-      if ((r++ % NT) != tile) continue;
+    const int n_todo = __popc(todo);
+    // round k: tile t takes the (k*NT + t)-th leftover op, so all tiles work
+    // side by side
+    for (int k = 0; k * NT < n_todo; ++k) {
+      const int rank = k * NT + tile;
+      if (rank >= n_todo) continue;
+      const int j = (int)__fns(todo, 0, rank + 1);
       const u64 Kj = sm.key[j];
       const u64 h1j = sm.h1[j], h2j = sm.h2[j];
-      const PreOp* pre = (((pre_mask >> j) & 1u) && sm.fresh[j]) ? &sm.pre[j] : nullptr;
+      const PreRef pre = (((pre_mask >> j) & 1u) && sm.fresh[j]) ? PreRef{&sm.pre, j} : no_pre();
       u64 o = 0;
       u8 sj;
       if (KIND == KIND_QUERY) {
