@@ -265,6 +265,63 @@ ws_status ws_batch_plan_destroy(ws_batch_plan* plan);
  * the GPU race, so order them on one stream.  Device pointers only. */
 ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n_items, ws_stream stream);
 
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching request loop over device-resident tables.
+ * A request is a mixed op batch (ws_mixed_op codes) on one table, with HOST
+ * buffers (pinned recommended) that must stay valid until its completion is
+ * polled.  A worker thread keeps up to max_inflight launches on the GPU; each
+ * launch runs the waiting requests of distinct tables (per-table FIFO, oldest
+ * first, at most one request per table in flight) in one persistent
+ * multi-table kernel.  Each result therefore equals that of replaying its
+ * table's requests alone in arrival order.  Tables are admitted only while
+ * free device memory stays above hbm_headroom of the total; a table about to
+ * pass grow_at load is rehashed into one twice as large when memory admits
+ * it.  plain = 1 serves one request per launch, one launch at a time (the
+ * per-request baseline). */
+typedef struct ws_server ws_server;
+typedef struct {
+  int32_t device;           /* -1 = current */
+  int32_t max_inflight;     /* launches in flight (default 4) */
+  uint64_t max_batch_ops;   /* ops per launch and per request (default 2^22) */
+  uint32_t max_batch_reqs;  /* requests per launch (default 256) */
+  int32_t plain;            /* 1: per-request launches, one at a time */
+  double hbm_headroom;      /* fraction of device memory kept free (default 0.05) */
+  double grow_at;           /* load that triggers growth; 0 = never grow */
+} ws_server_config;
+typedef struct {
+  uint32_t table;  /* id from ws_server_add_table */
+  uint32_t reserved;
+  const uint8_t* ops;
+  const uint64_t* keys;
+  const uint64_t* vals;  /* nullable: values 0 */
+  uint64_t* vals_out;    /* nullable */
+  uint8_t* status_out;   /* nullable */
+  uint64_t n;
+  uint64_t tag;          /* returned in the completion */
+} ws_request;
+typedef struct {
+  uint64_t id, tag;
+  double t_submit, t_start, t_done;  /* seconds on the steady clock */
+  int32_t status;
+  uint32_t table;
+} ws_completion;
+ws_status ws_server_create(const ws_server_config* cfg, ws_server** out);
+/* WS_ERR_OOM when free device memory does not admit the table. */
+ws_status ws_server_add_table(ws_server* s, uint64_t capacity, ws_scheme scheme, int metadata, int tile,
+                              uint32_t* id);
+/* Thread-safe; returns at once.  n <= max_batch_ops. */
+ws_status ws_server_submit(ws_server* s, const ws_request* r, uint64_t* id);
+/* Up to max completions (waits up to wait_ms for the first). */
+ws_status ws_server_poll(ws_server* s, ws_completion* out, uint64_t max, uint64_t* n_out, int wait_ms);
+/* Blocks until every submitted request has completed. */
+ws_status ws_server_drain(ws_server* s);
+/* The current table behind an id (changes when the table grows). */
+ws_status ws_server_table(ws_server* s, uint32_t id, ws_table** out);
+ws_status ws_server_stats(ws_server* s, uint64_t* submitted, uint64_t* completed, uint64_t* launches,
+                          uint64_t* grows);
+/* Finishes queued work, then frees the server and its tables. */
+ws_status ws_server_destroy(ws_server* s);
+
 /* Text of the last CUDA error seen by this library on the calling thread. */
 const char* ws_cuda_error_string(void);
 const char* ws_status_string(ws_status s);

@@ -17,7 +17,7 @@ from . import _lib
 
 __all__ = ["Table", "WsError", "SCHEMES", "UPSERT_OPS", "MISS", "FOUND", "INSERTED", "FAIL_FULL",
            "FAIL_BADKEY", "FAIL_TIMEOUT", "MX_QUERY", "MX_INSERT", "MX_ADD", "MX_MAX", "MX_REPLACE",
-           "MX_ERASE", "lib", "BatchPlan", "BK_INSERT", "BK_UPSERT", "BK_QUERY", "BK_ERASE"]
+           "MX_ERASE", "lib", "BatchPlan", "BK_INSERT", "BK_UPSERT", "BK_QUERY", "BK_ERASE", "Server"]
 
 SCHEMES = {"double": 0, "p2": 1}
 UPSERT_OPS = {"add": 0, "max": 1, "replace": 2, "insert": 3}
@@ -282,6 +282,105 @@ class BatchPlan:
     def close(self):
         if getattr(self, "_h", None):
             lib().ws_batch_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop over device-resident tables.
+
+    Requests are mixed op batches on one table with host buffers (numpy
+    arrays; pinned memory is fastest).  ``submit`` returns at once; outputs
+    are filled in when ``poll`` / ``drain`` report the request complete.
+    """
+
+    def __init__(self, max_inflight=4, max_batch_ops=1 << 22, max_batch_reqs=256, plain=False,
+                 hbm_headroom=0.05, grow_at=0.85, device=-1):
+        cfg = _lib.WsServerConfig(int(device), int(max_inflight), int(max_batch_ops), int(max_batch_reqs),
+                                  int(bool(plain)), float(hbm_headroom), float(grow_at))
+        h = ctypes.c_void_p()
+        _check(lib().ws_server_create(ctypes.byref(cfg), ctypes.byref(h)), "ws_server_create")
+        self._h = h
+        self._live = {}
+        self._done = {}
+
+    def add_table(self, capacity, scheme="double", metadata=False, tile=0) -> int:
+        i = ctypes.c_uint32()
+        _check(lib().ws_server_add_table(self._h, int(capacity), SCHEMES[scheme], int(bool(metadata)), int(tile),
+                                         ctypes.byref(i)), "ws_server_add_table")
+        return int(i.value)
+
+    def submit(self, table, ops, keys, vals=None, want_values=True, want_status=True, tag=0,
+               vals_out=None, status_out=None) -> int:
+        ops = np.ascontiguousarray(ops, dtype=np.uint8)
+        keys = np.ascontiguousarray(keys).view(np.uint64)
+        if vals is not None:
+            vals = np.ascontiguousarray(vals).view(np.uint64)
+        n = keys.size
+        vo = vals_out if vals_out is not None else (np.empty(n, np.uint64) if want_values else None)
+        so = status_out if status_out is not None else (np.empty(n, np.uint8) if want_status else None)
+        req = _lib.WsRequest(int(table), 0, _ptr(ops), _ptr(keys), _ptr(vals), _ptr(vo), _ptr(so), n, int(tag))
+        rid = ctypes.c_uint64()
+        _check(lib().ws_server_submit(self._h, ctypes.byref(req), ctypes.byref(rid)), "ws_server_submit")
+        self._live[int(rid.value)] = (ops, keys, vals, vo, so)
+        return int(rid.value)
+
+    def poll(self, max_n=4096, wait_ms=0):
+        buf = (_lib.WsCompletion * max_n)()
+        n = ctypes.c_uint64()
+        _check(lib().ws_server_poll(self._h, buf, max_n, ctypes.byref(n), int(wait_ms)), "ws_server_poll")
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            ops, keys, vals, vo, so = self._live.pop(int(c.id))
+            out.append({"id": int(c.id), "tag": int(c.tag), "t_submit": c.t_submit, "t_start": c.t_start,
+                        "t_done": c.t_done, "status": int(c.status), "table": int(c.table), "vals": vo,
+                        "st": so})
+        return out
+
+    def drain(self):
+        _check(lib().ws_server_drain(self._h), "ws_server_drain")
+        res = []
+        while True:
+            got = self.poll()
+            if not got:
+                break
+            res += got
+        return res
+
+    def table_handle(self, tid):
+        h = ctypes.c_void_p()
+        _check(lib().ws_server_table(self._h, int(tid), ctypes.byref(h)), "ws_server_table")
+        return h
+
+    def count(self, tid) -> int:
+        v = ctypes.c_uint64()
+        _check(lib().ws_count(self.table_handle(tid), ctypes.byref(v)), "ws_count")
+        return int(v.value)
+
+    def dump(self, tid):
+        h = self.table_handle(tid)
+        inf = _lib.WsInfo()
+        _check(lib().ws_table_info_get(h, ctypes.byref(inf)), "ws_table_info_get")
+        slots = np.empty((inf.slots, 2), dtype=np.uint64)
+        tags = np.empty(inf.slots, dtype=np.uint16) if inf.metadata else None
+        _check(lib().ws_dump(h, slots.ctypes.data, None if tags is None else tags.ctypes.data), "ws_dump")
+        return slots, tags
+
+    def stats(self):
+        a, b, c, d = (ctypes.c_uint64() for _ in range(4))
+        _check(lib().ws_server_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+               "ws_server_stats")
+        return {"submitted": a.value, "completed": b.value, "launches": c.value, "grows": d.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().ws_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

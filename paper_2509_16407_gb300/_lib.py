@@ -35,6 +35,24 @@ class WsBatchItem(ctypes.Structure):
                 ("n", ctypes.c_uint64)]
 
 
+class WsServerConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32), ("max_batch_ops", ctypes.c_uint64),
+                ("max_batch_reqs", ctypes.c_uint32), ("plain", ctypes.c_int32), ("hbm_headroom", ctypes.c_double),
+                ("grow_at", ctypes.c_double)]
+
+
+class WsRequest(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("ops", ctypes.c_void_p),
+                ("keys", ctypes.c_void_p), ("vals", ctypes.c_void_p), ("vals_out", ctypes.c_void_p),
+                ("status_out", ctypes.c_void_p), ("n", ctypes.c_uint64), ("tag", ctypes.c_uint64)]
+
+
+class WsCompletion(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("tag", ctypes.c_uint64), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("status", ctypes.c_int32),
+                ("table", ctypes.c_uint32)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "ws_table_create": (st, [u64, i32, i32, ctypes.POINTER(vp)]),
@@ -69,6 +87,15 @@ SIGNATURES = {
                                 ctypes.POINTER(ctypes.c_uint64)]),
     "ws_batch_plan_destroy": (st, [vp]),
     "ws_batch_run_noalloc": (st, [ctypes.POINTER(WsBatchItem), u64, vp]),
+    "ws_server_create": (st, [ctypes.POINTER(WsServerConfig), ctypes.POINTER(vp)]),
+    "ws_server_add_table": (st, [vp, u64, i32, i32, i32, ctypes.POINTER(ctypes.c_uint32)]),
+    "ws_server_submit": (st, [vp, ctypes.POINTER(WsRequest), ctypes.POINTER(ctypes.c_uint64)]),
+    "ws_server_poll": (st, [vp, ctypes.POINTER(WsCompletion), u64, ctypes.POINTER(ctypes.c_uint64), i32]),
+    "ws_server_drain": (st, [vp]),
+    "ws_server_table": (st, [vp, ctypes.c_uint32, ctypes.POINTER(vp)]),
+    "ws_server_stats": (st, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                             ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "ws_server_destroy": (st, [vp]),
     "ws_cuda_error_string": (ctypes.c_char_p, []),
     "ws_status_string": (ctypes.c_char_p, [i32]),
     "ws_version": (u32, []),

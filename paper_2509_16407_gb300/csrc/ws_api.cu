@@ -213,26 +213,10 @@ __global__ void primary_bucket_kernel(const u64* keys, u64* out, u64 n, u64 seed
 
 }  // namespace
 
-extern "C" {
-
-uint32_t ws_version(void) { return 0x000100u; }
-
-const char* ws_cuda_error_string(void) { return g_cuda_err; }
-
-const char* ws_status_string(ws_status s) {
-  switch (s) {
-    case WS_OK: return "ok";
-    case WS_ERR_INVALID: return "invalid argument";
-    case WS_ERR_INVALID_KEY: return "an op used a reserved sentinel key";
-    case WS_ERR_OOM: return "out of device memory";
-    case WS_ERR_FULL: return "an insert found no free slot";
-    case WS_ERR_TIMEOUT: return "an op hit the lock spin limit";
-    case WS_ERR_CUDA: return "CUDA error";
-  }
-  return "unknown status";
-}
-
-ws_status ws_table_create_ex(const ws_config* cfg, ws_table** out) {
+// Shared constructor.  With a stream, memory comes from the stream-ordered
+// allocator and is cleared on that stream (no device-wide synchronisation),
+// so a serving loop can grow a table while other work is in flight.
+ws_status wsi::table_create(const ws_config* cfg, cudaStream_t stream, ws_table** out) {
   if (!cfg || !out) return WS_ERR_INVALID;
   *out = nullptr;
   if (cfg->scheme != WS_DOUBLE && cfg->scheme != WS_P2) return WS_ERR_INVALID;
@@ -265,6 +249,8 @@ ws_status ws_table_create_ex(const ws_config* cfg, ws_table** out) {
   t->pmax = cfg->max_probe ? cfg->max_probe : kDefaultProbe;
   if ((u64)t->pmax > nb) t->pmax = (uint32_t)nb;
   t->spin = cfg->spin_limit ? cfg->spin_limit : kDefaultSpin;
+  t->stream_alloc = stream != nullptr;
+  t->last_stream = stream;
   if (cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     note_cuda(cudaGetLastError(), "cudaDeviceGetAttribute");
     delete t;
@@ -273,11 +259,14 @@ ws_status ws_table_create_ex(const ws_config* cfg, ws_table** out) {
   const u64 lock_words = (nb + 31) / 32;
   ws::TableView& tv = t->tv;
   std::memset(&tv, 0, sizeof(tv));
-  bool oom = cudaMalloc(&tv.slots, t->S * sizeof(ws::Slot)) != cudaSuccess;
-  if (!oom && meta) oom = cudaMalloc(&tv.tags, t->S * sizeof(uint16_t)) != cudaSuccess;
-  if (!oom) oom = cudaMalloc(&tv.locks, lock_words * 4) != cudaSuccess;
-  if (!oom) oom = cudaMalloc(&tv.ctr, sizeof(ws::Counters)) != cudaSuccess;
-  if (oom) {
+  auto alloc = [&](void** p, size_t bytes) {
+    return (stream ? cudaMallocAsync(p, bytes, stream) : cudaMalloc(p, bytes)) == cudaSuccess;
+  };
+  bool ok = alloc(reinterpret_cast<void**>(&tv.slots), t->S * sizeof(ws::Slot));
+  if (ok && meta) ok = alloc(reinterpret_cast<void**>(&tv.tags), t->S * sizeof(uint16_t));
+  if (ok) ok = alloc(reinterpret_cast<void**>(&tv.locks), lock_words * 4);
+  if (ok) ok = alloc(reinterpret_cast<void**>(&tv.ctr), sizeof(ws::Counters));
+  if (!ok) {
     cudaGetLastError();
     free_table_memory(t);
     delete t;
@@ -291,11 +280,14 @@ ws_status ws_table_create_ex(const ws_config* cfg, ws_table** out) {
   tv.spin_limit = t->spin;
   tv.shortcut = 1;
   tv.preload = kDefaultPreload;
-  cudaError_t e = cudaMemset(tv.slots, 0, t->S * sizeof(ws::Slot));
-  if (e == cudaSuccess && meta) e = cudaMemset(tv.tags, 0, t->S * 2);
-  if (e == cudaSuccess) e = cudaMemset(tv.locks, 0, lock_words * 4);
-  if (e == cudaSuccess) e = cudaMemset(tv.ctr, 0, sizeof(ws::Counters));
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  auto clear = [&](void* p, size_t bytes) {
+    return stream ? cudaMemsetAsync(p, 0, bytes, stream) : cudaMemset(p, 0, bytes);
+  };
+  cudaError_t e = clear(tv.slots, t->S * sizeof(ws::Slot));
+  if (e == cudaSuccess && meta) e = clear(tv.tags, t->S * 2);
+  if (e == cudaSuccess) e = clear(tv.locks, lock_words * 4);
+  if (e == cudaSuccess) e = clear(tv.ctr, sizeof(ws::Counters));
+  if (e == cudaSuccess && !stream) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     note_cuda(e, "table init");
     free_table_memory(t);
@@ -305,6 +297,50 @@ ws_status ws_table_create_ex(const ws_config* cfg, ws_table** out) {
   *out = t;
   return WS_OK;
 }
+
+// Stream-ordered release of a table made with a stream (no device sync);
+// a table made without one is released the ordinary way.
+void wsi::table_free_async(ws_table* t, cudaStream_t stream) {
+  if (!t) return;
+  if (!t->stream_alloc) {
+    ws_destroy(t);
+    return;
+  }
+  DeviceGuard guard(t->device);
+  void* ptrs[4] = {t->tv.slots, t->tv.tags, t->tv.locks, t->tv.ctr};
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, stream);
+  t->tv.slots = nullptr;
+  t->tv.tags = nullptr;
+  t->tv.locks = nullptr;
+  t->tv.ctr = nullptr;
+  if (t->stage) {
+    free_staging(t->stage);
+    t->stage = nullptr;
+  }
+  delete t;
+}
+
+extern "C" {
+
+uint32_t ws_version(void) { return 0x000100u; }
+
+const char* ws_cuda_error_string(void) { return g_cuda_err; }
+
+const char* ws_status_string(ws_status s) {
+  switch (s) {
+    case WS_OK: return "ok";
+    case WS_ERR_INVALID: return "invalid argument";
+    case WS_ERR_INVALID_KEY: return "an op used a reserved sentinel key";
+    case WS_ERR_OOM: return "out of device memory";
+    case WS_ERR_FULL: return "an insert found no free slot";
+    case WS_ERR_TIMEOUT: return "an op hit the lock spin limit";
+    case WS_ERR_CUDA: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+ws_status ws_table_create_ex(const ws_config* cfg, ws_table** out) { return wsi::table_create(cfg, nullptr, out); }
 
 ws_status ws_table_create(uint64_t capacity, ws_scheme scheme, int metadata, ws_table** out) {
   ws_config c;

@@ -64,6 +64,7 @@ struct ws_table {
   wsi::u64 bytes = 0;
   cudaStream_t last_stream = nullptr;
   wsi::Staging* stage = nullptr;
+  bool stream_alloc = false;  // memory from the stream-ordered allocator
 };
 
 namespace wsi {
@@ -72,4 +73,9 @@ cudaError_t dispatch(const ws_table* t, const ws::TableView& tv, const ws::Batch
 // 1 device pointer on `device`, 2 host, 3 another device, 0 null.
 int classify(const void* p, int device);
 enum { PTR_NULL = 0, PTR_DEVICE = 1, PTR_HOST = 2, PTR_OTHER_DEVICE = 3 };
+// Table constructor; with a non-null stream it allocates and clears on that
+// stream without synchronising the device.
+ws_status table_create(const ws_config* cfg, cudaStream_t stream, ws_table** out);
+// Free a table on a stream (for tables made with a stream).
+void table_free_async(ws_table* t, cudaStream_t stream);
 }  // namespace wsi

@@ -143,9 +143,9 @@ struct TileOps {
   // ----------------------------------------------------------------------
   // First-probe preload (one lane per op; see the file comment)
   // ----------------------------------------------------------------------
-  // Metadata second wave: the first slot of b_0 whose tag matches K, for op j.
-  __device__ static __forceinline__ void preload_candidate(const TableView& tv, u64 K, PreWarp* pw, int j) {
-    const u64 b0 = fmix64(K ^ tv.seed1) & tv.nb_mask;
+  // Metadata second copy of a wave: the first slot of bucket b whose tag
+  // matches K, for op j.
+  __device__ static __forceinline__ void preload_candidate(const TableView& tv, u64 K, u64 b0, PreWarp* pw, int j) {
     const u16 kt = key_tag(K);
     int q = -1;
 #pragma unroll
@@ -839,87 +839,92 @@ struct TileOps {
     }
   }
 
-  // Does the snapshot prove K absent (for a lock-free probe)?
-  __device__ static __forceinline__ bool snap_absent(const TableView& tv, const Snap& sn) {
-    if (sn.hit >= 0 || sn.unsure || !sn.empty) return false;
-    if (SCHEME == SCHEME_DOUBLE) return true;
-    return tv.shortcut && sn.occ < FILL_SHORTCUT && tv.nb_mask != 0;
-  }
+  // ----------------------------------------------------------------------
+  // Lane waves: the lane owning an op settles it bucket by bucket from
+  // snapshots of the probe sequence (wave w holds bucket w of every op still
+  // open), the same rules as the tile probe.  lane_wave returns 1 when the op
+  // is settled, 0 to go on to the next wave, -1 to hand it to the tile path
+  // (more than the snapshot can tell, a lost CAS, or a locked insert).
+  // ----------------------------------------------------------------------
+  enum { LW_QUERY = 0, LW_INSERT_FREE = 1, LW_UPDATE_ONLY = 2, LW_ERASE = 3 };
+  struct LaneState {
+    bool ff_set;  // first free slot of the probe sequence seen so far
+    u64 ff_idx, ff_k, ff_v;
+  };
 
-  __device__ static __forceinline__ bool lane_query(const TableView& tv, PreRef p, u64 K, u64 b0, u64& out,
-                                                    u8& st) {
+  __device__ static __forceinline__ int lane_wave(const TableView& tv, PreRef p, u64 K, u64 V, int op, int opk,
+                                                  u32 w, u64 bw, LaneState& ls, u64& out, u8& st, int& dcount,
+                                                  bool& fresh) {
     const Snap sn = snap_of(p, K);
-    if (sn.hit >= 0) {
-      u64 idx;
-      hit_pair(p, sn, b0, idx, out);
-      st = ST_FOUND;
-      return true;
-    }
-    if (snap_absent(tv, sn)) {
-      out = 0;
-      st = ST_MISS;
-      return true;
-    }
-    return false;
-  }
-
-  // Upsert: a hit is updated in place; with LOCKFREE double hashing an absent
-  // key is claimed into the first free slot of b_0 (it precedes the EMPTY
-  // slot that ended the existence scan, so it is the first free slot of the
-  // probe sequence).
-  template <bool LOCKFREE>
-  __device__ static __forceinline__ bool lane_upsert(const TableView& tv, PreRef p, u64 K, u64 b0, u64 V, int op,
-                                                     u8& st, int& dcount, bool& fresh) {
-    const Snap sn = snap_of(p, K);
+    if (sn.unsure) return -1;
     if (sn.hit >= 0) {
       u64 idx, v;
-      hit_pair(p, sn, b0, idx, v);
-      apply(tv, idx, op, V);
-      st = ST_FOUND;
-      return true;
-    }
-    if (!(LOCKFREE && SCHEME == SCHEME_DOUBLE) || !snap_absent(tv, sn) || sn.ffree < 0) return false;
-    const u64 fi = b0 * B + (u64)sn.ffree;
-    bool ok;
-    if (META) {
-      const u16 expect = sn.ffree_empty ? TAG_EMPTY : TAG_TOMB;
-      ok = ptx::cas_tag(tv.tags + fi, expect, key_tag(K)) == expect;
-      if (ok) ptx::st_slot_release(tv.slots + fi, K, V);
-    } else {
-      const Slot o = p.slot(sn.ffree);
-      ok = ptx::cas_slot(tv.slots + fi, o.key, o.val, K, V);
-    }
-    if (!ok) {
-      fresh = false;
-      return false;
-    }
-    ++dcount;
-    st = ST_INSERTED;
-    return true;
-  }
-
-  __device__ static __forceinline__ bool lane_erase(const TableView& tv, PreRef p, u64 K, u64 b0, u64& out,
-                                                    u8& st, int& dcount, bool& fresh) {
-    const Snap sn = snap_of(p, K);
-    if (sn.hit >= 0) {
-      u64 idx, v;
-      hit_pair(p, sn, b0, idx, v);
+      hit_pair(p, sn, bw, idx, v);
+      if (opk == LW_QUERY) {
+        out = v;
+        st = ST_FOUND;
+        return 1;
+      }
+      if (opk != LW_ERASE) {
+        apply(tv, idx, op, V);
+        st = ST_FOUND;
+        return 1;
+      }
       if (!ptx::cas_slot(tv.slots + idx, K, v, KEY_TOMB, 0)) {
         fresh = false;
-        return false;
+        return -1;
       }
       if (META) ptx::st_tag_release(tv.tags + idx, TAG_TOMB);
       out = v;
       --dcount;
       st = ST_FOUND;
-      return true;
+      return 1;
     }
-    if (snap_absent(tv, sn)) {
+    // no K in what the snapshot shows; with plain buckets wider than the
+    // snapshot an EMPTY slot in it still settles the whole bucket (EMPTY
+    // slots form a suffix of the bucket)
+    if (!META && PRE_SLOTS < B && !sn.empty) return -1;
+    if (opk == LW_INSERT_FREE && !ls.ff_set && sn.ffree >= 0) {
+      ls.ff_set = true;
+      if (META) {
+        ls.ff_idx = bw * 32 + (u64)sn.ffree;
+        ls.ff_k = sn.ffree_empty ? TAG_EMPTY : TAG_TOMB;
+      } else {
+        const Slot o = p.slot(sn.ffree);
+        ls.ff_idx = bw * B + (u64)sn.ffree;
+        ls.ff_k = o.key;
+        ls.ff_v = o.val;
+      }
+    }
+    const u32 P = nprobe(tv);
+    bool ends;
+    if (SCHEME == SCHEME_DOUBLE)
+      ends = sn.empty || w + 1 >= P;
+    else
+      ends = (w + 1 >= P) || (w == 0 && tv.shortcut && sn.occ < FILL_SHORTCUT);
+    if (!ends) return 0;
+    if (opk == LW_QUERY || opk == LW_ERASE) {
+      if (SCHEME == SCHEME_DOUBLE && !sn.empty) return -1;  // probe cap reached: let the tiles confirm
       out = 0;
       st = ST_MISS;
-      return true;
+      return 1;
     }
-    return false;
+    if (opk != LW_INSERT_FREE || !sn.empty || !ls.ff_set) return -1;
+    bool ok;
+    if (META) {
+      const u16 expect = (u16)ls.ff_k;
+      ok = ptx::cas_tag(tv.tags + ls.ff_idx, expect, key_tag(K)) == expect;
+      if (ok) ptx::st_slot_release(tv.slots + ls.ff_idx, K, V);
+    } else {
+      ok = ptx::cas_slot(tv.slots + ls.ff_idx, ls.ff_k, ls.ff_v, K, V);
+    }
+    if (!ok) {
+      fresh = false;
+      return -1;
+    }
+    ++dcount;
+    st = ST_INSERTED;
+    return 1;
   }
 };
 
@@ -949,7 +954,8 @@ constexpr int kWarps = kThreads / 32;
 
 struct WarpSmem {
   u64 key[32], val[32], out[32], h1[32], h2[32];
-  u8 op[32], st[32], fresh[32], pad[32];
+  u64 bw[32];  // bucket of each op in the current wave
+  u8 op[32], st[32], fresh[32], snapw[32];
   PreWarp pre;
 };
 
@@ -966,83 +972,100 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
   const u64 V = ((KIND == KIND_UPSERT || KIND == KIND_MIXED) && inb && a.vals) ? a.vals[gi * ks] : 0;
   const u8 code = (KIND == KIND_MIXED && inb) ? a.ops[gi] : 0;
   const u64 h1 = fmix64(K ^ tv.seed1), h2 = fmix64(K ^ tv.seed2);
-  const u64 b0 = h1 & tv.nb_mask;
   sm.key[lane] = K;
   sm.val[lane] = V;
   sm.op[lane] = code;
   sm.h1[lane] = h1;
   sm.h2[lane] = h2;
   const bool skip = (KIND == KIND_UPSERT) && (a.flags & BATCH_SKIP_SENTINELS) && is_sentinel(K);
-  const bool pre_ok = (KIND != KIND_PROBE) && tv.preload && inb && !is_sentinel(K);
-  const unsigned pre_mask = __ballot_sync(0xffffffffu, pre_ok);
   __syncwarp();
-  if (KIND != KIND_PROBE && tv.preload) {
-    // first probe of every op, 16 bytes per lane per instruction
+
+  // what the lane path may do for this op
+  int dcount = 0;
+  bool done = !inb;
+  bool fresh = true;
+  u64 out = 0;
+  u8 st = ST_MISS;
+  int opk = -1, op = upsert_op;
+  if (inb && skip) {
+    done = true;  // an empty / erased slot of a rehash source
+  } else if (inb && is_sentinel(K)) {
+    done = true;
+    st = ST_BADKEY;
+  } else if (inb) {
+    int kind = KIND;
+    if (KIND == KIND_MIXED) {
+      kind = code == MX_QUERY ? KIND_QUERY : code == MX_ERASE ? KIND_ERASE : KIND_UPSERT;
+      op = code == MX_INSERT ? OP_INSERT : code == MX_ADD ? OP_ADD : code == MX_MAX ? OP_MAX : OP_REPLACE;
+      if (code > MX_ERASE) {
+        done = true;
+        st = ST_BADKEY;
+      }
+    }
+    if (!done) {
+      if (kind == KIND_QUERY)
+        opk = Ops::LW_QUERY;
+      else if (kind == KIND_ERASE)
+        opk = Ops::LW_ERASE;
+      else if (KIND == KIND_UPSERT && lockfree && SCHEME == SCHEME_DOUBLE)
+        opk = Ops::LW_INSERT_FREE;
+      else
+        opk = Ops::LW_UPDATE_ONLY;
+    }
+  }
+
+  // lane waves: wave w copies bucket w of every op still open into shared
+  // memory (16 bytes per lane per copy instruction, coalesced per bucket),
+  // then each lane settles its own op if the snapshot allows
+  bool lane_ok = (KIND != KIND_PROBE) && tv.preload && opk >= 0;
+  typename Ops::LaneState ls;
+  ls.ff_set = false;
+  ls.ff_idx = ls.ff_k = ls.ff_v = 0;
+  int snap_wave = -1;
+  constexpr u32 kMaxWaves = (SCHEME == SCHEME_DOUBLE) ? 4u : 2u;
+  for (u32 w = 0; w < kMaxWaves; ++w) {
+    const bool want = lane_ok && !done;
+    const unsigned wmask = __ballot_sync(0xffffffffu, want);
+    if (!wmask) break;
+    sm.bw[lane] = want ? Ops::bucket(tv, h1, h2, w) : 0;
+    __syncwarp();
     if (META) {
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int j = i * 8 + (lane >> 2), part = lane & 3;
-        if ((pre_mask >> j) & 1u) {
-          const u64 bj = sm.h1[j] & tv.nb_mask;
-          ptx::cp_async16(&sm.pre.line[part][j], tv.tags + bj * 32 + 8 * part);
-        }
+        if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.line[part][j], tv.tags + sm.bw[j] * 32 + 8 * part);
       }
     } else {
       constexpr int PS = Ops::PRE_SLOTS;  // 8 slots = 128 B per op
 #pragma unroll
       for (int i = 0; i < PS; ++i) {
         const int j = i * (32 / PS) + lane / PS, part = lane % PS;
-        if ((pre_mask >> j) & 1u) {
-          const u64 bj = sm.h1[j] & tv.nb_mask;
-          ptx::cp_async16(&sm.pre.line[part][j], tv.slots + bj * B + (u64)part);
-        }
+        if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.line[part][j], tv.slots + sm.bw[j] * B + (u64)part);
       }
     }
     ptx::cp_async_wait_all();
     __syncwarp();
     if (META) {
-      if (pre_ok) Ops::preload_candidate(tv, K, &sm.pre, lane);
+      if (want) Ops::preload_candidate(tv, K, sm.bw[lane], &sm.pre, lane);
       ptx::cp_async_wait_all();
       __syncwarp();
     }
-  }
-
-  // lane fast path (each lane counts its own op's count delta)
-  int dcount = 0;
-  bool done = !inb;
-  bool fresh = true;
-  u64 out = 0;
-  u8 st = ST_MISS;
-  if (inb && skip) {
-    done = true;  // an empty / erased slot of a rehash source
-  } else if (inb && is_sentinel(K)) {
-    done = true;
-    st = ST_BADKEY;
-  } else if (pre_ok) {
-    const PreRef p{&sm.pre, lane};
-    int kind = KIND;
-    int op = upsert_op;
-    if (KIND == KIND_MIXED) {
-      kind = code == MX_QUERY ? KIND_QUERY : code == MX_ERASE ? KIND_ERASE : KIND_UPSERT;
-      op = code == MX_INSERT ? OP_INSERT : code == MX_ADD ? OP_ADD : code == MX_MAX ? OP_MAX : OP_REPLACE;
-      if (code > MX_ERASE) {
-        kind = -1;
+    if (want) {
+      snap_wave = (int)w;
+      const PreRef p{&sm.pre, lane};
+      const int r = Ops::lane_wave(tv, p, K, V, op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh);
+      if (r > 0)
         done = true;
-        st = ST_BADKEY;
-      }
+      else if (r < 0)
+        lane_ok = false;
     }
-    if (kind == KIND_QUERY)
-      done = Ops::lane_query(tv, p, K, b0, out, st);
-    else if (kind == KIND_ERASE)
-      done = Ops::lane_erase(tv, p, K, b0, out, st, dcount, fresh);
-    else if (kind == KIND_UPSERT)
-      done = (KIND == KIND_UPSERT && lockfree)
-                 ? Ops::template lane_upsert<true>(tv, p, K, b0, V, op, st, dcount, fresh)
-                 : Ops::template lane_upsert<false>(tv, p, K, b0, V, op, st, dcount, fresh);
+    __syncwarp();  // the next wave overwrites the snapshots
   }
+  // the tile path may reuse a snapshot only if it is still of b_0 and fresh
+  const unsigned pre_mask = __ballot_sync(0xffffffffu, snap_wave == 0 && fresh);
   sm.out[lane] = out;
   sm.st[lane] = st;
-  sm.fresh[lane] = fresh ? 1 : 0;
+  sm.fresh[lane] = 1;
   if (done && inb && st >= ST_FULL) count_failure(tv, st);
   const unsigned todo = __ballot_sync(0xffffffffu, !done);
   __syncwarp();

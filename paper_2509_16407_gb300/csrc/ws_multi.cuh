@@ -17,7 +17,7 @@ constexpr int kMultiChunk = kWarps * 32;  // ops per chunk = one block iteration
 struct MultiItem {
   TableView tv;
   BatchArgs a;
-  int kind;      // KIND_QUERY / KIND_UPSERT / KIND_ERASE
+  int kind;      // KIND_QUERY / KIND_UPSERT / KIND_ERASE / KIND_MIXED (per-op codes in a.ops)
   int cfg;       // index into the menu
   int lockfree;  // no erase of this table in this phase
   int pad;
@@ -50,6 +50,8 @@ __device__ __forceinline__ int multi_warp(const MultiItem& it, u64 base, WarpSme
     return warp_chunk<SCHEME, META, B, T, KIND_QUERY>(it.tv, it.a, 0, false, base, sm, lane);
   if (it.kind == KIND_UPSERT)
     return warp_chunk<SCHEME, META, B, T, KIND_UPSERT>(it.tv, it.a, it.a.op, it.lockfree != 0, base, sm, lane);
+  if (it.kind == KIND_MIXED)
+    return warp_chunk<SCHEME, META, B, T, KIND_MIXED>(it.tv, it.a, 0, false, base, sm, lane);
   return warp_chunk<SCHEME, META, B, T, KIND_ERASE>(it.tv, it.a, 0, false, base, sm, lane);
 }
 

@@ -139,9 +139,12 @@ def zipf(seed: int, n: int, N: int, s: float) -> np.ndarray:
 
 
 def rank_to_key(ranks: np.ndarray, universe_seed: int = 0) -> np.ndarray:
-    """Bijective map of ranks (>= 1) to uniform-looking non-zero keys."""
+    """Bijective map of ranks (1 <= rank < 2^40) to uniform-looking non-zero
+    keys: the splitmix64 finaliser of rank + universe_seed * 2^40 (never 0, so
+    the finaliser never returns 0)."""
     r = np.asarray(ranks, dtype=np.uint64)
-    k = mix13(r ^ np.uint64(universe_seed))
+    with np.errstate(over="ignore"):
+        k = mix13(r + np.uint64(universe_seed) * np.uint64(1 << 40))
     if ((k == np.uint64(0)) | (k >= np.uint64((1 << 64) - 2))).any():
         raise ValueError("rank_to_key produced a sentinel; choose another universe seed")
     return k
@@ -210,3 +213,48 @@ def log_uniform_int(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
     u = uniform01(seed, n)
     v = np.exp2(np.log2(lo) + u * (np.log2(hi) - np.log2(lo)))
     return np.clip(np.floor(v), lo, hi).astype(np.int64)
+
+
+def mixed_request(seed: int, n: int, universe: int, universe_seed: int, s: float = 0.99,
+                  fracs=(0.6, 0.3, 0.05, 0.05)):
+    """One serving request of ``n`` ops on one table: Zipf(s) keys over the
+    table's ``universe`` ranks (keys bijective in the rank and
+    ``universe_seed``), op classes query / upsert-add / insert / erase with
+    quotas ``fracs``.  A key's class is fixed for the request by a splitmix64
+    draw of key ^ seed mod 20 (12 query, 6 add, 1 insert, 1 erase), so the
+    classes are key-disjoint; draws are kept in order while their class has
+    quota.  Returns (ops u8, keys u64, vals u64)."""
+    quota = [int(round(n * f)) for f in fracs]
+    quota[0] += n - sum(quota)
+    codes = (MX_QUERY, MX_ADD, MX_INSERT, MX_ERASE)
+    bounds = (12, 18, 19, 20)
+    ops_parts, key_parts = [], []
+    rnd = 0
+    while sum(quota) > 0:
+        m = max(64, int(sum(quota) * 1.5))
+        ranks = zipf(seed * 7 + 1 + rnd * 1000003, m, universe, s)
+        rnd += 1
+        keys = rank_to_key(ranks, universe_seed)
+        c20 = (mix13(keys ^ np.uint64(seed & ((1 << 64) - 1))) % np.uint64(20)).astype(np.int64)
+        cls = np.searchsorted(np.array(bounds), c20, side="right")
+        keep = np.zeros(m, bool)
+        for ci in range(4):
+            if quota[ci] <= 0:
+                continue
+            idx = np.nonzero(cls == ci)[0][: quota[ci]]
+            keep[idx] = True
+            quota[ci] -= idx.size
+        ops_parts.append(np.array(codes, np.uint8)[cls[keep]])
+        key_parts.append(keys[keep])
+        if rnd > 200:  # a class whose keys carry almost no Zipf mass: fill with queries
+            if sum(quota) > 0:
+                extra = sum(quota)
+                r2 = zipf(seed + 99, extra, universe, s)
+                ops_parts.append(np.full(extra, MX_QUERY, np.uint8))
+                k2 = rank_to_key(r2, universe_seed)
+                key_parts.append(k2)
+            break
+    ops = np.concatenate(ops_parts)[:n]
+    keys = np.concatenate(key_parts)[:n]
+    vals = uniform_int(seed + 0x77, n, 1, 1000)
+    return ops, keys, vals
