@@ -53,7 +53,9 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--sweep", default="", help="write the load/tile sweep as JSON lines to this file")
     p.add_argument("--sweep-log2-slots", default="28,22")
-    p.add_argument("--workload", default="config2", choices=["config2", "batched", "serve"],
+    p.add_argument("--aging-log2-slots", type=int, default=26)
+    p.add_argument("--aging-iters", type=int, default=300)
+    p.add_argument("--workload", default="config2", choices=["config2", "batched", "serve", "aging"],
                    help="config2 = the default line; batched = 1024 uneven tables in one graph launch")
     p.add_argument("--tables", type=int, default=1024)
     p.add_argument("--requests", type=int, default=600, help="serve: requests per run")
@@ -122,6 +124,24 @@ class ClockSampler:
 def to_dev(a, dev):
     import torch
     return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).to(dev, non_blocking=False)
+
+
+def splitmix_torch(seed, n, start, dev):
+    """The splitmix64 stream (positions start .. start+n-1) computed on the
+    device in wrapping int64 arithmetic (same bits as workloads.splitmix64)."""
+    import torch
+    def s64(x):
+        x &= (1 << 64) - 1
+        return x - (1 << 64) if x >= 1 << 63 else x
+    def srl(z, k):
+        return (z >> k) & ((1 << (64 - k)) - 1)
+    z = torch.arange(start + 1, start + n + 1, dtype=torch.int64, device=dev) * s64(0x9E3779B97F4A7C15) + s64(seed)
+    z = (z ^ srl(z, 30)) * s64(0xBF58476D1CE4E5B9)
+    z = (z ^ srl(z, 27)) * s64(0x94D049BB133111EB)
+    z = z ^ srl(z, 31)
+    if bool(((z == 0) | (z == -1) | (z == -2)).any()):
+        raise RuntimeError("sentinel drawn from the key stream; pick another seed")
+    return z
 
 
 def gen_dev(seed, n, start, dev, chunk=1 << 24):
@@ -648,6 +668,8 @@ def bench_serve(args):
         ids = [sv.add_table(int(c)) for c in caps]
         outs = [(pinned(np.empty(r[2].size, np.uint64)), pinned(np.empty(r[2].size, np.uint8))) for r in reqs]
         torch.cuda.synchronize()
+        if arrivals is None:
+            sv.pause()  # saturation: the whole burst is queued before the clock starts
         t0 = time.monotonic()
         rid = []
         for i, (t, ops, keys, vals) in enumerate(reqs):
@@ -656,6 +678,8 @@ def bench_serve(args):
                 while time.monotonic() < target:
                     pass
             rid.append(sv.submit(ids[t], ops, keys, vals, vals_out=outs[i][0], status_out=outs[i][1]))
+        if arrivals is None:
+            t0 = time.monotonic()
         done = {c["id"]: c for c in sv.drain()}
         t_end = max(c["t_done"] for c in done.values())
         if arrivals is not None:
@@ -692,6 +716,70 @@ def bench_serve(args):
             "config": {"workload": "config 5: 64 tables 2^16-2^26 slots, request sizes log-uniform 1-2^20, "
                                    "60/30/5/5 query/add/insert/erase, Zipf(0.99) keys, host (pinned) buffers",
                        "data": "synthetic"}}
+
+
+# ---------------------------------------------------------------------------
+# aging (paper §6.4): fill to 85%, then per iteration ONE mixed kernel that
+# inserts 1% new keys, erases the oldest 1%, and queries 1% present and 1%
+# absent keys; probe counts (ws_probe_cost) beside the paper's Table 1
+# aging column.
+# ---------------------------------------------------------------------------
+TABLE1_AGING = {"DoubleHT": (77.09, 1.61, 80.00, 4.57), "DoubleHT(M)": (23.52, 2.10, 19.39, 6.12),
+                "P2HT": (11.02, 3.96, 8.01, 6.85), "P2HT(M)": (6.02, 2.42, 2.01, 6.4)}
+
+
+def bench_aging(args):
+    import torch
+    import paper_2509_16407_gb300 as ws
+    dev = torch.device("cuda", 0)
+    S = 1 << args.aging_log2_slots
+    m = S // 100
+    fill = int(0.85 * S)
+    iters = args.aging_iters
+    pool = splitmix_torch(0xA61, fill + iters * m + m, 0, dev)
+    negp = splitmix_torch(0xB62, iters * m, 0, dev)
+    ops = torch.tensor([ws.MX_INSERT, ws.MX_ERASE, ws.MX_QUERY, ws.MX_QUERY], dtype=torch.uint8,
+                       device=dev).repeat(m)
+    out = {}
+    for scheme, meta, name in DESIGNS:
+        t = ws.Table(S, scheme, meta)
+        t.insert(pool[:fill], pool[:fill] * 3)
+        times, probes = [], {}
+        for it in range(iters):
+            ins = pool[fill + it * m: fill + (it + 1) * m]
+            era = pool[it * m: (it + 1) * m]
+            pos = pool[(it + 1) * m: (it + 2) * m]
+            neg = negp[it * m: (it + 1) * m]
+            if it in (0, iters // 2, iters - 1):
+                costs = {}
+                for ph, k in (("insert", ins), ("positive", pos), ("negative", neg), ("delete", era)):
+                    c, _ = t.probe_cost(k[: 1 << 16])
+                    costs[ph] = round(float((c.cpu().numpy().view(np.uint64) >> np.uint64(32)).mean()), 3)
+                probes[it] = costs
+            keys = torch.stack([ins, era, pos, neg], 1).reshape(-1).contiguous()
+            vals = torch.stack([ins * 3, torch.zeros_like(ins), torch.zeros_like(ins), torch.zeros_like(ins)],
+                               1).reshape(-1).contiguous()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            t.mixed(ops, keys, vals, return_values=False, return_status=False)
+            b.record()
+            times.append((a, b))
+        torch.cuda.synchronize()
+        ms = np.array([a.elapsed_time(b) for a, b in times])
+        cnt = t.count()
+        err = t.last_error()
+        out[name] = {"gops_mean": round(4 * m / ms.mean() / 1e6, 3), "gops_first10": round(4 * m / ms[:10].mean() / 1e6, 3),
+                     "gops_last10": round(4 * m / ms[-10:].mean() / 1e6, 3), "iter_ms_p50": round(float(np.median(ms)), 4),
+                     "iter_ms_p99": round(float(np.percentile(ms, 99)), 4), "count_after": cnt, "count_expected": fill,
+                     "failed_ops": err, "probe_lines": probes,
+                     "paper_table1_aging_probes(ins,pos,neg,del)": TABLE1_AGING[name]}
+        t.close()
+        torch.cuda.empty_cache()
+    return {"metric": "aging Gops/s (all ops of an iteration in one kernel) and probe lines per op", "unit": UNIT,
+            "value": round(float(np.mean([v["gops_mean"] for v in out.values()])), 4), "higher_is_better": True,
+            "designs": out, "config": {"workload": f"aging: 2^{args.aging_log2_slots} slots, fill 0.85, {iters} "
+                                                    f"iterations of 1% insert / 1% erase oldest / 1% + 1% queries",
+                                       "data": "synthetic"}}
 
 
 # ---------------------------------------------------------------------------
@@ -774,6 +862,9 @@ def main():
         return
     if args.workload == "batched":
         print(json.dumps(bench_batched(args)), flush=True)
+        return
+    if args.workload == "aging":
+        print(json.dumps(bench_aging(args)), flush=True)
         return
     if args.workload == "serve":
         print(json.dumps(bench_serve(args)), flush=True)

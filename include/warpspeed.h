@@ -313,7 +313,11 @@ ws_status ws_server_add_table(ws_server* s, uint64_t capacity, ws_scheme scheme,
 ws_status ws_server_submit(ws_server* s, const ws_request* r, uint64_t* id);
 /* Up to max completions (waits up to wait_ms for the first). */
 ws_status ws_server_poll(ws_server* s, ws_completion* out, uint64_t max, uint64_t* n_out, int wait_ms);
-/* Blocks until every submitted request has completed. */
+/* Stop (paused != 0) or resume admitting requests into new launches; work
+ * already on the GPU continues.  Lets a caller queue a burst first. */
+ws_status ws_server_pause(ws_server* s, int paused);
+/* Resumes a paused server, then blocks until every submitted request has
+ * completed. */
 ws_status ws_server_drain(ws_server* s);
 /* The current table behind an id (changes when the table grows). */
 ws_status ws_server_table(ws_server* s, uint32_t id, ws_table** out);

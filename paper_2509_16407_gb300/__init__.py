@@ -343,6 +343,9 @@ class Server:
                         "st": so})
         return out
 
+    def pause(self, paused=True):
+        _check(lib().ws_server_pause(self._h, int(bool(paused))), "ws_server_pause")
+
     def drain(self):
         _check(lib().ws_server_drain(self._h), "ws_server_drain")
         res = []

@@ -92,6 +92,7 @@ SIGNATURES = {
     "ws_server_submit": (st, [vp, ctypes.POINTER(WsRequest), ctypes.POINTER(ctypes.c_uint64)]),
     "ws_server_poll": (st, [vp, ctypes.POINTER(WsCompletion), u64, ctypes.POINTER(ctypes.c_uint64), i32]),
     "ws_server_drain": (st, [vp]),
+    "ws_server_pause": (st, [vp, i32]),
     "ws_server_table": (st, [vp, ctypes.c_uint32, ctypes.POINTER(vp)]),
     "ws_server_stats": (st, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),

@@ -95,6 +95,7 @@ struct ws_server {
   std::condition_variable cv_work, cv_done;
   std::thread worker;
   bool stop = false;
+  bool paused = false;
   int error = 0;
 };
 
@@ -308,6 +309,7 @@ void worker_main(ws_server* sv) {
     }
     if (progress) sv->cv_done.notify_all();
     for (Slot& sl : sv->slots) {
+      if (sv->paused && !sv->stop) break;
       if (sl.busy) continue;
       if (!launch_slot(sv, sl)) break;
       progress = true;
@@ -431,9 +433,18 @@ ws_status ws_server_poll(ws_server* sv, ws_completion* out, uint64_t max, uint64
   return sv->error ? (ws_status)sv->error : WS_OK;
 }
 
+ws_status ws_server_pause(ws_server* sv, int paused) {
+  if (!sv) return WS_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  sv->paused = paused != 0;
+  sv->cv_work.notify_one();
+  return WS_OK;
+}
+
 ws_status ws_server_drain(ws_server* sv) {
   if (!sv) return WS_ERR_INVALID;
   std::unique_lock<std::mutex> lk(sv->mu);
+  sv->paused = false;  // draining a paused server would wait forever
   sv->cv_work.notify_one();
   sv->cv_done.wait(lk, [&] { return sv->n_completed == sv->n_submitted; });
   return sv->error ? (ws_status)sv->error : WS_OK;

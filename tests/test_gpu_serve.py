@@ -38,9 +38,11 @@ def _requests(n_req, seed):
     return out
 
 
-def _serve(ws, reqs, **kw):
+def _serve(ws, reqs, burst=False, **kw):
     sv = ws.Server(**kw)
     ids = [sv.add_table(c, sch, m, t) for (c, sch, m, t) in TABLES]
+    if burst:
+        sv.pause()  # queue everything first: launches must then batch requests
     rid = [sv.submit(ids[t], ops, keys, vals) for (t, ops, keys, vals) in reqs]
     done = {c["id"]: c for c in sv.drain()}
     assert len(done) == len(reqs) and all(c["status"] == 0 for c in done.values())
@@ -75,11 +77,13 @@ def _same(reqs, a, b):
 
 def test_serving_equals_solo_replay_plain_and_oracle(ws, oracle_mod):
     reqs = _requests(160, 5)
-    cont, cont_contents, st = _serve(ws, reqs, max_inflight=4, max_batch_reqs=64, grow_at=0.5)
-    assert st["grows"] >= 1 and st["launches"] < len(reqs)
-    plain, plain_contents, st_p = _serve(ws, reqs, plain=True, grow_at=0.5)
+    cont, cont_contents, st = _serve(ws, reqs, burst=True, max_inflight=4, max_batch_reqs=64, grow_at=0.5)
+    assert st["grows"] >= 1 and st["launches"] < len(reqs) // 2
+    trickle, trickle_contents, _ = _serve(ws, reqs, max_inflight=4, grow_at=0.5)  # requests as they come
+    plain, plain_contents, st_p = _serve(ws, reqs, burst=True, plain=True, grow_at=0.5)
     assert st_p["launches"] == len(reqs)
     _same(reqs, cont, plain)
+    _same(reqs, cont, trickle)
     # solo replay: each table's requests alone, in arrival order, one ws_mixed call each
     solo = [None] * len(reqs)
     oracle_res = [None] * len(reqs)
@@ -93,7 +97,7 @@ def test_serving_equals_solo_replay_plain_and_oracle(ws, oracle_mod):
             solo[i] = (host(gv), host(gs))
             oracle_res[i] = om.mixed(ops, keys, vals)
         ok, ov = om.items()
-        for contents in (cont_contents, plain_contents):
+        for contents in (cont_contents, plain_contents, trickle_contents):
             assert (contents[ti][0] == ok).all() and (contents[ti][1] == ov).all()
         t.close()
     _same(reqs, cont, solo)
