@@ -135,7 +135,13 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  metadata the bucket's tag line and first tag-matching slot -- into shared
  *  memory with asynchronous copies, so 32 first probes per warp are in flight
  *  at once.  0 reads everything with plain loads. */
-enum { WS_OPT_PRELOAD = 1 };
+/*  WS_OPT_PHASED (default 0): bulk-synchronous mode, the paper's "phased"
+ *  tables of the concurrency-overhead benchmark (§6.2): probes use weak
+ *  L1-cacheable loads and absent-key inserts take no lock.  Valid only for
+ *  calls whose keys are distinct and whose probed slots nothing else writes
+ *  during the call (e.g. a pure query batch, or inserts of distinct new
+ *  keys); otherwise results are undefined. */
+enum { WS_OPT_PRELOAD = 1, WS_OPT_PHASED = 2 };
 ws_status ws_set_option(ws_table* t, int option, int64_t value);
 
 /* Insert-if-unique (§5.1 Upsert with the empty callback).  status_out: per-op

@@ -147,6 +147,10 @@ class Table:
         """First-probe preload into shared memory (on by default)."""
         _check(lib().ws_set_option(self._h, 1, int(bool(on))), "ws_set_option")
 
+    def set_phased(self, on: bool):
+        """Bulk-synchronous mode (weak cacheable loads, no locks; distinct keys only)."""
+        _check(lib().ws_set_option(self._h, 2, int(bool(on))), "ws_set_option")
+
     def clear(self, stream=None):
         _check(lib().ws_clear(self._h, self._stream(stream)), "ws_clear")
 

@@ -407,6 +407,10 @@ ws_status ws_set_option(ws_table* t, int option, int64_t value) {
       if (value != 0 && value != 1) return WS_ERR_INVALID;
       t->tv.preload = (int)value;
       return WS_OK;
+    case WS_OPT_PHASED:
+      if (value != 0 && value != 1) return WS_ERR_INVALID;
+      t->tv.phased = (int)value;
+      return WS_OK;
   }
   return WS_ERR_INVALID;
 }

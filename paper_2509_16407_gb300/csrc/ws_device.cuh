@@ -58,6 +58,7 @@ struct TableView {
   u32 spin_limit; // lock attempts before giving up
   int shortcut;   // P2: no erase ever ran, so the primary-fill shortcut is exact
   int preload;    // stage each op's first probe into shared memory with async copies (1) or not (0)
+  int phased;     // bulk-synchronous mode: weak cacheable probe loads, no locks (see WS_OPT_PHASED)
 };
 
 struct BatchArgs {
@@ -119,6 +120,15 @@ __device__ __forceinline__ void st_slot_release(Slot* p, u64 k, u64 v) {
       "st.release.gpu.global.b128 [%0], t;\n\t}" ::"l"(p),
       "l"(k), "l"(v)
       : "memory");
+}
+
+// Weak (L1-cacheable) loads for the bulk-synchronous mode: valid only while
+// nothing writes what they read during the launch.
+__device__ __forceinline__ void ld_slot_weak(const Slot* p, u64& k, u64& v) {
+  asm volatile("ld.global.v2.u64 {%0, %1}, [%2];" : "=l"(k), "=l"(v) : "l"(p) : "memory");
+}
+__device__ __forceinline__ void ld_tags16_weak(const u16* p, u64& a, u64& b) {
+  asm volatile("ld.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 
 // 128-bit compare-and-swap of a whole slot (relaxed: the pair itself is the

@@ -182,7 +182,10 @@ struct TileOps {
       k = s.key;
       v = s.val;
     } else {
-      ptx::ld_slot(tv.slots + si, k, v);
+      if (tv.phased)
+        ptx::ld_slot_weak(tv.slots + si, k, v);
+      else
+        ptx::ld_slot(tv.slots + si, k, v);
     }
   }
 
@@ -366,7 +369,10 @@ struct TileOps {
       for (int q = 0; q < TPL; ++q) t[q] = sp[q];
     } else if (TPL == 8) {
       u64 a0, a1;
-      ptx::ld_tags16(tp, a0, a1);
+      if (tv.phased)
+        ptx::ld_tags16_weak(tp, a0, a1);
+      else
+        ptx::ld_tags16(tp, a0, a1);
 #pragma unroll
       for (int q = 0; q < TPL; ++q) t[q] = (u16)(((q < 4) ? (a0 >> (16 * q)) : (a1 >> (16 * (q - 4)))) & 0xffffu);
     } else if (TPL == 4) {
@@ -397,7 +403,12 @@ struct TileOps {
                                                    u64& v) {
     k = 0;
     v = 0;
-    if (c.tl == 0) ptx::ld_slot(tv.slots + si, k, v);
+    if (c.tl == 0) {
+      if (tv.phased)
+        ptx::ld_slot_weak(tv.slots + si, k, v);
+      else
+        ptx::ld_slot(tv.slots + si, k, v);
+    }
     k = c.shfl(k, 0);
     v = c.shfl(v, 0);
   }
@@ -693,7 +704,8 @@ struct TileOps {
     // present its slot never moves, so the update needs no lock.  This keeps
     // a batch's many copies of a hot key from queueing on one lock bit.
     const u64 b0 = bucket(tv, h1, h2, 0);
-    for (u32 tries = 0, ns = 0;;) {
+    // bulk-synchronous mode: distinct keys per call, nothing to serialise
+    for (u32 tries = 0, ns = 0; !tv.phased;) {
       if (try_lock(tv, c, b0)) break;
       const Hit again = find(tv, c, K, h1, h2, no_pre());
       if (again.found) {
@@ -721,7 +733,7 @@ struct TileOps {
         break;
       }
     }
-    unlock(tv, c, b0);
+    if (!tv.phased) unlock(tv, c, b0);
     return st;
   }
 

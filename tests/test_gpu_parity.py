@@ -160,7 +160,12 @@ def test_config2_small(ws, oracle_mod, scheme, meta, tile, load):
     uost = om.upsert(ukeys, uvals, 0)
     ufull = ust == ws.FAIL_FULL
     if ufull.any():
-        assert scheme == "p2" and load > 0.9
+        # the new keys take two-choice tables past 0.9 load: a key whose both
+        # buckets are taken fails, and the layout must show both full
+        assert scheme == "p2" and load >= 0.9 and ufull.mean() < 0.02
+        r, L = check_layout(oracle_mod, t)
+        assert oracle_mod.candidates_full(L["slots"], L["tags"], L["nb"], L["B"], L["scheme"], L["pmax"],
+                                          L["seed1"], L["seed2"], ukeys[ufull]).all()
         om.erase(ukeys[ufull])
     assert ((ust == uost) | ufull).all()
     # erase 10%, then query everything again
