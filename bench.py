@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--sweep-log2-slots", default="28,22")
     p.add_argument("--aging-log2-slots", type=int, default=26)
     p.add_argument("--aging-iters", type=int, default=300)
-    p.add_argument("--workload", default="config2", choices=["config2", "batched", "serve", "aging"],
+    p.add_argument("--workload", default="config2", choices=["config2", "batched", "serve", "aging", "phased"],
                    help="config2 = the default line; batched = 1024 uneven tables in one graph launch")
     p.add_argument("--tables", type=int, default=1024)
     p.add_argument("--requests", type=int, default=600, help="serve: requests per run")
@@ -783,6 +783,69 @@ def bench_aging(args):
 
 
 # ---------------------------------------------------------------------------
+# cost of concurrency (paper §6.2, Table 1 right block): the same queries and
+# inserts with the concurrent protocol and in bulk-synchronous (phased) mode
+# -- weak cacheable loads, no locks -- on 2^28-slot tables at 0.9 load.
+# ---------------------------------------------------------------------------
+TABLE1_PHASED = {"DoubleHT": (3166, 3233), "DoubleHT(M)": (2624, 2624), "P2HT": (1471, 1471), "P2HT(M)": (2903, 2909)}
+
+
+def bench_phased(args):
+    import torch
+    import paper_2509_16407_gb300 as ws
+    dev = torch.device("cuda", 0)
+    S = 1 << args.log2_slots
+    base_n, top_n = int(0.85 * S), int(0.9 * S)
+    nq = args.nq
+    keys = splitmix_torch(0xD0D0, top_n + nq, 0, dev)
+    vals = keys * 3
+    slice_k, neg = keys[base_n:top_n], keys[top_n:]
+    pos = keys[:top_n][torch.from_numpy((W.splitmix64(7, nq) % np.uint64(top_n)).astype(np.int64)).to(dev)]
+    out_q = torch.empty(nq, dtype=torch.int64, device=dev)
+    res = {}
+
+    def tm(f, reps=3):
+        best = 1e30
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        return best
+
+    for scheme, meta, name in DESIGNS:
+        t = ws.Table(S, scheme, meta)
+        t.insert(keys[:base_n], vals[:base_n])
+        r = {}
+        for phased in (False, True):
+            t.set_phased(phased)
+            ins = tm(lambda: (t.insert(slice_k, vals[base_n:top_n]), t.erase(slice_k)), reps=2)
+            t.set_phased(False)
+            t.insert(slice_k, vals[base_n:top_n])
+            t.set_phased(phased)
+            qp = tm(lambda: t.query(pos, out=out_q))
+            qn = tm(lambda: t.query(neg, out=out_q))
+            t.set_phased(False)
+            t.erase(slice_k)
+            key = "phased" if phased else "concurrent"
+            r[key] = {"query_gops": round(2 * nq / (qp + qn) / 1e6, 3), "query_pos_gops": round(nq / qp / 1e6, 3),
+                      "query_neg_gops": round(nq / qn / 1e6, 3),
+                      "insert_erase_pair_gops": round((top_n - base_n) / ins / 1e6, 3)}
+        r["query_overhead_pct"] = round(100 * (1 - r["concurrent"]["query_gops"] / r["phased"]["query_gops"]), 2)
+        r["paper_table1_concurrent_phased_mops(A40)"] = TABLE1_PHASED[name]
+        res[name] = r
+        t.close()
+        torch.cuda.empty_cache()
+    return {"metric": "query Gops/s, concurrent vs phased (bulk-synchronous) mode", "unit": UNIT,
+            "value": round(float(np.mean([v["concurrent"]["query_gops"] for v in res.values()])), 4),
+            "higher_is_better": True, "designs": res,
+            "config": {"workload": f"2^{args.log2_slots} slots at 0.9 load, {nq} positive + {nq} negative queries, "
+                                   "5% slice insert+erase", "data": "synthetic"}}
+
+
+# ---------------------------------------------------------------------------
 # load / tile sweep (config 2): one JSON line per (slots, design, tile, load)
 # ---------------------------------------------------------------------------
 def sweep(args):
@@ -862,6 +925,9 @@ def main():
         return
     if args.workload == "batched":
         print(json.dumps(bench_batched(args)), flush=True)
+        return
+    if args.workload == "phased":
+        print(json.dumps(bench_phased(args)), flush=True)
         return
     if args.workload == "aging":
         print(json.dumps(bench_aging(args)), flush=True)
