@@ -223,7 +223,9 @@ def mixed_request(seed: int, n: int, universe: int, universe_seed: int, s: float
     quotas ``fracs``.  A key's class is fixed for the request by a splitmix64
     draw of key ^ seed mod 20 (12 query, 6 add, 1 insert, 1 erase), so the
     classes are key-disjoint; draws are kept in order while their class has
-    quota.  Returns (ops u8, keys u64, vals u64)."""
+    quota.  All inserts of one key carry the same value, so the result does
+    not depend on which concurrent copy wins.  Returns (ops u8, keys u64,
+    vals u64)."""
     quota = [int(round(n * f)) for f in fracs]
     quota[0] += n - sum(quota)
     codes = (MX_QUERY, MX_ADD, MX_INSERT, MX_ERASE)
@@ -246,15 +248,14 @@ def mixed_request(seed: int, n: int, universe: int, universe_seed: int, s: float
             quota[ci] -= idx.size
         ops_parts.append(np.array(codes, np.uint8)[cls[keep]])
         key_parts.append(keys[keep])
-        if rnd > 200:  # a class whose keys carry almost no Zipf mass: fill with queries
-            if sum(quota) > 0:
-                extra = sum(quota)
-                r2 = zipf(seed + 99, extra, universe, s)
-                ops_parts.append(np.full(extra, MX_QUERY, np.uint8))
-                k2 = rank_to_key(r2, universe_seed)
-                key_parts.append(k2)
-            break
+        if rnd == 200:  # a class whose keys carry almost no Zipf mass: its quota goes to queries
+            quota[0] += sum(quota[1:])
+            quota[1:] = [0, 0, 0]
     ops = np.concatenate(ops_parts)[:n]
     keys = np.concatenate(key_parts)[:n]
     vals = uniform_int(seed + 0x77, n, 1, 1000)
+    # insert-if-unique copies of one key carry one value (derived from the
+    # key): which copy wins is a race, the stored value is not
+    ins = ops == MX_INSERT
+    vals[ins] = mix13(keys[ins] ^ np.uint64(0x1D5)) % np.uint64(999) + np.uint64(1)
     return ops, keys, vals
