@@ -630,6 +630,29 @@ struct TileOps {
     if (c.tl == 0) ptx::red_and_release(tv.locks + (b >> 5), ~(1u << (b & 31)));
   }
 
+  // One lock attempt by a single lane (no test first: one round trip).  A
+  // lane that finds the bit set owns nothing and must not unlock.
+  __device__ static __forceinline__ bool lane_lock(const TableView& tv, u64 b) {
+    const u32 bit = 1u << (b & 31);
+    return !(ptx::atom_or_acquire(tv.locks + (b >> 5), bit) & bit);
+  }
+  __device__ static __forceinline__ void lane_unlock(const TableView& tv, u64 b) {
+    ptx::red_and_release(tv.locks + (b >> 5), ~(1u << (b & 31)));
+  }
+
+  // Two-choice placement (§4.2) from both buckets' loads and first free
+  // slots: b_0 while it is below 3/4, else the less loaded bucket (ties to
+  // b_0); the other bucket when the chosen one has no free slot.  Returns
+  // 0 / 1, or -1 when both are full.  have1 = false: only b_0 was read (the
+  // shortcut proved the key absent from b_1, or there is one bucket).
+  __device__ static __forceinline__ int p2_choice(u32 occ0, bool free0, u32 occ1, bool free1, bool have1) {
+    if (!have1) return free0 ? 0 : -1;
+    int ch = (occ0 < FILL_SHORTCUT) ? 0 : (occ1 < occ0 ? 1 : 0);
+    if (ch == 0 && !free0) ch = 1;
+    else if (ch == 1 && !free1) ch = 0;
+    return (ch == 0 ? free0 : free1) ? ch : -1;
+  }
+
   // ----------------------------------------------------------------------
   // Operations (tile-uniform control flow; results valid on every lane).
   // pre: the op's first-probe snapshot, or null.
@@ -858,10 +881,14 @@ struct TileOps {
   // is settled, 0 to go on to the next wave, -1 to hand it to the tile path
   // (more than the snapshot can tell, a lost CAS, or a locked insert).
   // ----------------------------------------------------------------------
-  enum { LW_QUERY = 0, LW_INSERT_FREE = 1, LW_UPDATE_ONLY = 2, LW_ERASE = 3 };
+  // LW_INSERT_FREE: lock-free first-free insert (double hashing, no erase
+  // in the launch).  LW_INSERT_LOCKED: the lane holds b_0's lock (or the
+  // launch is bulk-synchronous), so its snapshots are authoritative for K.
+  enum { LW_QUERY = 0, LW_INSERT_FREE = 1, LW_UPDATE_ONLY = 2, LW_ERASE = 3, LW_INSERT_LOCKED = 4 };
   struct LaneState {
     bool ff_set;  // first free slot of the probe sequence seen so far
     u64 ff_idx, ff_k, ff_v;
+    u32 occ0;     // two-choice: load of b_0 (wave 0)
   };
 
   __device__ static __forceinline__ int lane_wave(const TableView& tv, PreRef p, u64 K, u64 V, int op, int opk,
@@ -896,7 +923,9 @@ struct TileOps {
     // snapshot an EMPTY slot in it still settles the whole bucket (EMPTY
     // slots form a suffix of the bucket)
     if (!META && PRE_SLOTS < B && !sn.empty) return -1;
-    if (opk == LW_INSERT_FREE && !ls.ff_set && sn.ffree >= 0) {
+    const bool ins = (opk == LW_INSERT_FREE || opk == LW_INSERT_LOCKED);
+    if (SCHEME == SCHEME_P2 && w == 0) ls.occ0 = sn.occ;
+    if (ins && !ls.ff_set && sn.ffree >= 0 && (SCHEME == SCHEME_DOUBLE || w == 0)) {
       ls.ff_set = true;
       if (META) {
         ls.ff_idx = bw * 32 + (u64)sn.ffree;
@@ -921,14 +950,37 @@ struct TileOps {
       st = ST_MISS;
       return 1;
     }
-    if (opk != LW_INSERT_FREE || !sn.empty || !ls.ff_set) return -1;
+    if (!ins) return -1;
+    u64 fidx = ls.ff_idx, fk = ls.ff_k, fv = ls.ff_v;
+    if (SCHEME == SCHEME_DOUBLE) {
+      if (!sn.empty || !ls.ff_set) return -1;
+    } else {
+      // K is absent from its buckets and the lane holds b_0's lock: place it
+      const bool free0 = (w == 0) ? sn.ffree >= 0 : ls.ff_set;
+      const int ch = p2_choice(ls.occ0, free0, sn.occ, sn.ffree >= 0, w > 0);
+      if (ch < 0) {
+        st = ST_FULL;
+        return 1;
+      }
+      if (ch == (int)w) {  // the free slot of this wave's bucket
+        if (META) {
+          fidx = bw * 32 + (u64)sn.ffree;
+          fk = sn.ffree_empty ? TAG_EMPTY : TAG_TOMB;
+        } else {
+          const Slot o = p.slot(sn.ffree);
+          fidx = bw * B + (u64)sn.ffree;
+          fk = o.key;
+          fv = o.val;
+        }
+      }
+    }
     bool ok;
     if (META) {
-      const u16 expect = (u16)ls.ff_k;
-      ok = ptx::cas_tag(tv.tags + ls.ff_idx, expect, key_tag(K)) == expect;
-      if (ok) ptx::st_slot_release(tv.slots + ls.ff_idx, K, V);
+      const u16 expect = (u16)fk;
+      ok = ptx::cas_tag(tv.tags + fidx, expect, key_tag(K)) == expect;
+      if (ok) ptx::st_slot_release(tv.slots + fidx, K, V);
     } else {
-      ok = ptx::cas_slot(tv.slots + ls.ff_idx, ls.ff_k, ls.ff_v, K, V);
+      ok = ptx::cas_slot(tv.slots + fidx, fk, fv, K, V);
     }
     if (!ok) {
       fresh = false;
@@ -952,12 +1004,15 @@ __device__ __forceinline__ void count_failure(const TableView& tv, u8 st) {
 // One warp serves a chunk of up to 32 consecutive ops.
 //  1. Stage: lane j loads op j's key (value, op code) with coalesced loads and
 //     hashes it once; keys and hashes go to shared memory.
-//  2. Preload: the first probe of all 32 ops is copied into shared memory
+//  2. Lock: an op that may have to insert under the lock (two-choice
+//     inserts, mixed batches) takes b_0's lock from its lane, one attempt.
+//  3. Lane path: wave w copies bucket w of every open op into shared memory
 //     (cp.async; four ops' 128-byte lines per instruction, so each copy
-//     instruction is coalesced), and with metadata a second wave fetches
-//     each op's first tag-matching slot.
-//  3. Lane fast path: lane j settles op j from the snapshot when it can.
-//  4. Tiles serve the ops left over, dealt round-robin, with the cooperative
+//     instruction is coalesced; with metadata the 64-byte tag line, then the
+//     first tag-matching slot), and lane j settles op j from the snapshot
+//     when it can.  Two-choice tables with plain 32-slot buckets instead
+//     read whole buckets, eight per round, scanned by the warp's votes.
+//  4. Tiles serve the ops left over, side by side, with the cooperative
 //     probe (snapshot reused unless a lane CAS showed it stale).
 //  5. Results leave through shared memory as coalesced stores.
 // -------------------------------------------------------------------------
@@ -967,7 +1022,7 @@ constexpr int kWarps = kThreads / 32;
 struct WarpSmem {
   u64 key[32], val[32], out[32], h1[32], h2[32];
   u64 bw[32];  // bucket of each op in the current wave
-  u8 op[32], st[32], fresh[32], snapw[32];
+  u8 op[32], st[32], fresh[32], list[32];  // list: open ops of a bucket pass
   PreWarp pre;
 };
 
@@ -1026,15 +1081,138 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     }
   }
 
+  bool lane_ok = (KIND != KIND_PROBE) && tv.preload && opk >= 0;
+  // two-choice tables with plain 32-slot buckets read whole buckets instead
+  // of first-line snapshots (below)
+  constexpr bool kRounds = (SCHEME == SCHEME_P2) && !META && B == 32;
+  // An op that may insert an absent key under the lock takes b_0's lock
+  // from its own lane, one attempt; the lane's reads after it are then
+  // authoritative for K (only holders of b_0's lock insert K).  A lane that
+  // misses the lock leaves absent keys to the tiles, which wait for it.
+  constexpr bool kLaneLock = (SCHEME == SCHEME_DOUBLE) || META || Ops::PRE_SLOTS == B || kRounds;
+  const u64 b0 = Ops::bucket(tv, h1, h2, 0);
+  bool locked = false;
+  if (kLaneLock && lane_ok && !done && opk == Ops::LW_UPDATE_ONLY) {
+    locked = tv.phased || Ops::lane_lock(tv, b0);  // bulk-synchronous: no locks
+    if (locked) opk = Ops::LW_INSERT_LOCKED;
+  }
+  int snap_wave = -1;
+
+  if (kRounds) {
+    // Whole-bucket rounds: eight buckets per round, one op's bucket per copy
+    // instruction (lane s copies slot s), each scanned with two votes.
+    // Pass 0 reads b_0 of every open op, pass 1 b_1 of the ops still open;
+    // the lane owning an op settles it, and hands it to the tiles after a
+    // lost CAS or when it must insert without the lock.
+    bool open = lane_ok && !done;
+    u32 occ0 = 0;
+    int f0 = -1;
+    u64 f0k = 0, f0v = 0;
+    for (u32 c = 0; c < 2; ++c) {
+      const unsigned om = __ballot_sync(0xffffffffu, open);
+      if (!om) break;
+      if (open) {
+        sm.bw[lane] = Ops::bucket(tv, h1, h2, c);
+        sm.list[__popc(om & ((1u << lane) - 1u))] = (u8)lane;
+      }
+      __syncwarp();
+      const int n = __popc(om);
+      int hs = -1, fs = -1;
+      u32 occ = 0;
+      u64 hv = 0, fk = 0, fv = 0;
+      for (int r0 = 0; r0 < n; r0 += 8) {
+        const int nr = (n - r0) < 8 ? (n - r0) : 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+          if (q < nr) ptx::cp_async16(&sm.pre.line[q][lane], tv.slots + sm.bw[sm.list[r0 + q]] * 32 + (u64)lane);
+        ptx::cp_async_wait_all();
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q >= nr) break;  // warp-uniform
+          const int j = sm.list[r0 + q];
+          const u64 k = sm.pre.line[q][lane].key;
+          const unsigned mk = __ballot_sync(0xffffffffu, k == sm.key[j]);
+          const unsigned mf = __ballot_sync(0xffffffffu, k == KEY_EMPTY || k == KEY_TOMB);
+          if (lane == j) {
+            occ = 32u - (u32)__popc(mf);
+            if (mk) {
+              hs = __ffs(mk) - 1;
+              hv = sm.pre.line[q][hs].val;
+            }
+            if (mf) {
+              fs = __ffs(mf) - 1;
+              const Slot f = sm.pre.line[q][fs];
+              fk = f.key;
+              fv = f.val;
+            }
+          }
+        }
+        __syncwarp();  // the next round overwrites the rows
+      }
+      if (!open) continue;
+      const u64 bc = sm.bw[lane];
+      bool absent = false;
+      if (hs >= 0) {
+        const u64 idx = bc * 32 + (u64)hs;
+        open = false;
+        if (opk == Ops::LW_QUERY) {
+          out = hv;
+          st = ST_FOUND;
+          done = true;
+        } else if (opk == Ops::LW_ERASE) {
+          if (ptx::cas_slot(tv.slots + idx, K, hv, KEY_TOMB, 0)) {
+            out = hv;
+            --dcount;
+            st = ST_FOUND;
+            done = true;
+          }
+        } else {
+          Ops::apply(tv, idx, op, V);
+          st = ST_FOUND;
+          done = true;
+        }
+      } else if (c == 0) {
+        occ0 = occ;
+        f0 = fs;
+        f0k = fk;
+        f0v = fv;
+        absent = Ops::nprobe(tv) == 1 || (tv.shortcut && occ < Ops::FILL_SHORTCUT);
+      } else {
+        absent = true;
+      }
+      if (absent) {
+        open = false;
+        if (opk == Ops::LW_QUERY || opk == Ops::LW_ERASE) {
+          out = 0;
+          st = ST_MISS;
+          done = true;
+        } else if (opk == Ops::LW_INSERT_LOCKED) {
+          const int ch = Ops::p2_choice(occ0, f0 >= 0, occ, fs >= 0, c == 1);
+          if (ch < 0) {
+            st = ST_FULL;
+            done = true;
+          } else {
+            const u64 idx = ch == 0 ? b0 * 32 + (u64)f0 : bc * 32 + (u64)fs;
+            if (ptx::cas_slot(tv.slots + idx, ch == 0 ? f0k : fk, ch == 0 ? f0v : fv, K, V)) {
+              ++dcount;
+              st = ST_INSERTED;
+              done = true;
+            }
+          }
+        }
+      }
+    }
+  }
+
   // lane waves: wave w copies bucket w of every op still open into shared
   // memory (16 bytes per lane per copy instruction, coalesced per bucket),
   // then each lane settles its own op if the snapshot allows
-  bool lane_ok = (KIND != KIND_PROBE) && tv.preload && opk >= 0;
   typename Ops::LaneState ls;
   ls.ff_set = false;
   ls.ff_idx = ls.ff_k = ls.ff_v = 0;
-  int snap_wave = -1;
-  constexpr u32 kMaxWaves = (SCHEME == SCHEME_DOUBLE) ? 4u : 2u;
+  ls.occ0 = 0;
+  constexpr u32 kMaxWaves = kRounds ? 0u : (SCHEME == SCHEME_DOUBLE) ? 4u : 2u;
   for (u32 w = 0; w < kMaxWaves; ++w) {
     const bool want = lane_ok && !done;
     const unsigned wmask = __ballot_sync(0xffffffffu, want);
@@ -1073,6 +1251,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     }
     __syncwarp();  // the next wave overwrites the snapshots
   }
+  if (locked && !tv.phased) Ops::lane_unlock(tv, b0);  // after the claim (release)
   // the tile path may reuse a snapshot only if it is still of b_0 and fresh
   const unsigned pre_mask = __ballot_sync(0xffffffffu, snap_wave == 0 && fresh);
   sm.out[lane] = out;
