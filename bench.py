@@ -33,6 +33,10 @@ import workloads as W  # noqa: E402
 
 DESIGNS = [("double", False, "DoubleHT"), ("double", True, "DoubleHT(M)"), ("p2", False, "P2HT"),
            ("p2", True, "P2HT(M)")]
+# the front-yard / backyard table: not one of the four designs of the default
+# line; selectable with --designs and part of the aging / phased comparisons
+ICEBERG = ("iceberg", True, "IcebergHT(M)")
+ALL_DESIGNS = DESIGNS + [ICEBERG]
 METRIC = "Gops/s insert/query/upsert at 0.9 load; % of HBM roofline; serve p50/p99 latency"
 UNIT = "Gops/s"
 PHASES = ["insert", "query_pos", "query_neg", "upsert_add", "erase"]
@@ -41,7 +45,7 @@ PHASES = ["insert", "query_pos", "query_neg", "upsert_add", "erase"]
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--log2-slots", type=int, default=28)
@@ -59,8 +63,9 @@ def parse():
                    help="config2 = the default line; batched = 1024 uneven tables in one graph launch")
     p.add_argument("--tables", type=int, default=1024)
     p.add_argument("--requests", type=int, default=600, help="serve: requests per run")
-    p.add_argument("--tiles", default="auto", choices=["auto", "paper"],
-                   help="auto: per design, the tile size with the fastest step (measured before timing)")
+    p.add_argument("--tiles", default="auto", choices=["auto", "paper", "4", "8", "16", "32"],
+                   help="auto: per design, the tile size with the fastest step (measured before timing); "
+                        "paper: each design's tile from the paper; a number: that tile for every design")
     return p.parse_args()
 
 
@@ -81,7 +86,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
         except (FileNotFoundError, OSError):
@@ -185,14 +190,37 @@ def peak_gbs():
         return 6800.0, "fallback"
 
 
+def kernel_source_hash():
+    """Hash of the CUDA sources: recorded DRAM traffic is valid only for the
+    kernels it was measured on."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2509_16407_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def recorded_traffic():
-    """Per-launch DRAM traffic of the dominant kernel from a committed ncu summary."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    """Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of
+    each design:phase:tile kernel at the default workload, from the committed
+    ncu summary; empty when the kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_2p28.txt")
+    out, src = {}, None
     try:
         with open(path) as f:
-            return json.load(f)
-    except (OSError, ValueError):
+            for ln in f:
+                ln = ln.split("#", 1)[0].split()
+                if len(ln) == 2 and ln[0] == "source_hash":
+                    src = ln[1]
+                elif len(ln) == 2 and ln[0].count(":") == 2:  # design:phase:tile bytes
+                    out[ln[0]] = float(ln[1])
+    except OSError:
         return {}
+    return out if src == kernel_source_hash() else {}
 
 
 # ---------------------------------------------------------------------------
@@ -209,7 +237,7 @@ def bench_ours(args, rank, world):
     top_n = int(args.load * S)
     slice_n = top_n - base_n
     nq = args.nq
-    designs = DESIGNS if args.designs == "all" else [d for d in DESIGNS if d[2] in args.designs.split(",")]
+    designs = DESIGNS if args.designs == "all" else [d for d in ALL_DESIGNS if d[2] in args.designs.split(",")]
     seed = 0x5EED + 7919 * rank
 
     # device-resident inputs (one key stream: base | slice | absent)
@@ -246,6 +274,9 @@ def bench_ours(args, rank, world):
         t.erase(keys_slice)
 
     tuning = {}
+    if args.tiles not in ("auto", "paper"):
+        for name, t in tables:
+            t.set_tile(int(args.tiles))
     if args.tiles == "auto":
         # the paper keeps each design's fastest (bucket, tile) combination;
         # here: the tile with the fastest step, measured once per design
@@ -301,6 +332,10 @@ def bench_ours(args, rank, world):
     sample = 1 << 20
     costs = {}
     for name, t in tables:
+        # counted with one cache line per probe step (T = 8, or B when smaller),
+        # the method's own line count; a wider tile reads ahead speculatively
+        t_run = t.info()["tile"]
+        t.set_tile(min(8, t.info()["bucket_slots"]))
         c = {}
         cs, _ = t.probe_cost(keys_slice[:sample])  # insert scan cost at 0.85 load
         c["insert"] = cs
@@ -310,6 +345,7 @@ def bench_ours(args, rank, world):
         c["upsert_add"], _ = t.probe_cost(keys_up[:sample])
         c["erase"], _ = t.probe_cost(keys_slice[:sample])
         t.erase(keys_slice)
+        t.set_tile(t_run)
         torch.cuda.synchronize()
         costs[name] = {}
         for ph, v in c.items():
@@ -379,8 +415,8 @@ def bench_ours(args, rank, world):
                     "query_neg": "batch_kernel<KIND_QUERY>", "upsert_add": "batch_kernel<KIND_UPSERT, op=add>",
                     "erase": "batch_kernel<KIND_ERASE>"}
     tr = recorded_traffic()
-    dom_key = f"{dom[0]}:{dom[1]}"
-    traffic = tr.get(dom_key, {}).get("dram_bytes_per_launch") if tr.get("valid_for_commit") else None
+    tile_of = {name: t.info()["tile"] for name, t in tables}
+    traffic = tr.get(f"{dom[0]}:{dom[1]}:{tile_of[dom[0]]}")
     roofline = {"bound": "hbm", "achieved": round(dom[3], 1), "peak": peak, "unit": "GB/s",
                 "frac": round(dom[3] / peak, 4), "traffic": traffic,
                 "kernel": f"{dom[0]} {dom[1]}: {kernel_names[dom[1]]}",
@@ -724,7 +760,8 @@ def bench_serve(args):
 # absent keys; probe counts (ws_probe_cost) beside the paper's Table 1
 # aging column.
 # ---------------------------------------------------------------------------
-TABLE1_AGING = {"DoubleHT": (77.09, 1.61, 80.00, 4.57), "DoubleHT(M)": (23.52, 2.10, 19.39, 6.12),
+TABLE1_AGING = {"IcebergHT(M)": (6.98, 2.2, 3.02, 6.22),
+                "DoubleHT": (77.09, 1.61, 80.00, 4.57), "DoubleHT(M)": (23.52, 2.10, 19.39, 6.12),
                 "P2HT": (11.02, 3.96, 8.01, 6.85), "P2HT(M)": (6.02, 2.42, 2.01, 6.4)}
 
 
@@ -741,7 +778,7 @@ def bench_aging(args):
     ops = torch.tensor([ws.MX_INSERT, ws.MX_ERASE, ws.MX_QUERY, ws.MX_QUERY], dtype=torch.uint8,
                        device=dev).repeat(m)
     out = {}
-    for scheme, meta, name in DESIGNS:
+    for scheme, meta, name in ALL_DESIGNS:
         t = ws.Table(S, scheme, meta)
         t.insert(pool[:fill], pool[:fill] * 3)
         times, probes = [], {}
@@ -787,7 +824,8 @@ def bench_aging(args):
 # inserts with the concurrent protocol and in bulk-synchronous (phased) mode
 # -- weak cacheable loads, no locks -- on 2^28-slot tables at 0.9 load.
 # ---------------------------------------------------------------------------
-TABLE1_PHASED = {"DoubleHT": (3166, 3233), "DoubleHT(M)": (2624, 2624), "P2HT": (1471, 1471), "P2HT(M)": (2903, 2909)}
+TABLE1_PHASED = {"DoubleHT": (3166, 3233), "DoubleHT(M)": (2624, 2624), "P2HT": (1471, 1471), "P2HT(M)": (2903, 2909),
+                 "IcebergHT(M)": (2598, 2866)}
 
 
 def bench_phased(args):
@@ -815,7 +853,7 @@ def bench_phased(args):
             best = min(best, a.elapsed_time(b))
         return best
 
-    for scheme, meta, name in DESIGNS:
+    for scheme, meta, name in ALL_DESIGNS:
         t = ws.Table(S, scheme, meta)
         t.insert(keys[:base_n], vals[:base_n])
         r = {}
@@ -862,7 +900,7 @@ def sweep(args):
         keys = gen_dev(0xABC + lg, top + nq, 0, dev)
         vals = keys * 3
         neg = keys[top:]
-        for scheme, meta, name in DESIGNS:
+        for scheme, meta, name in ALL_DESIGNS:
             for tile in (4, 8, 16, 32):
                 t = ws.Table(S, scheme, meta, tile=tile)
                 have = 0

@@ -61,7 +61,14 @@ extern "C" {
 typedef struct ws_table ws_table;       /* opaque; owned by the library */
 typedef struct CUstream_st* ws_stream;  /* identical to cudaStream_t */
 
-typedef enum { WS_DOUBLE = 0, WS_P2 = 1 } ws_scheme;
+/* Probe schemes (§2.2): DOUBLE = double hashing over up to max_probe buckets;
+ * P2 = two choices, primary bucket while below 3/4 full, else the less loaded;
+ * ICEBERG = front yard / backyard (§2.2, split as in the table list of §5):
+ * about 83% of the buckets form a front yard probed by single hashing, the
+ * rest a backyard probed by two choices; a key goes to its front bucket while
+ * that has a free slot, else to the less loaded of its two backyard buckets.
+ * ICEBERG needs metadata (IcebergHT(M)) and at least 4 buckets. */
+typedef enum { WS_DOUBLE = 0, WS_P2 = 1, WS_ICEBERG = 2 } ws_scheme;
 
 /* Upsert callbacks of §5.1: ADD = atomicAdd (wrapping mod 2^64), MAX = u64 max,
  * REPLACE = overwrite, INSERT = the empty callback (insert-if-unique). */
@@ -88,10 +95,16 @@ enum { WS_MISS = 0, WS_FOUND = 1, WS_INSERTED = 2, WS_FAIL_FULL = 3, WS_FAIL_BAD
 /* Full configuration; ws_table_create() fills the paper's defaults (§5):
  *  DoubleHT: 8-slot buckets (one 128-byte line), tile 8; DoubleHT(M): 32-slot
  *  buckets, tile 4; P2HT: 32-slot buckets (four lines), tile 8; P2HT(M): 32,
- *  tile 4.  bucket_slots in {8, 16, 32} (32 when metadata != 0); tile in
- *  {4, 8, 16, 32}.  max_probe = number of buckets a double-hashing probe
- *  sequence may visit (default 80, clamped to the bucket count); ignored by P2.
- *  The bucket count is capacity / bucket_slots rounded up to a power of two. */
+ *  tile 4; IcebergHT(M): 32, tile 4.  bucket_slots in {8, 16, 32} (32 when
+ *  metadata != 0); tile in {4, 8, 16, 32}.  max_probe = number of buckets a
+ *  double-hashing probe sequence may visit (default 80, clamped to the bucket
+ *  count); ignored by the other schemes.  The bucket count nb is capacity /
+ *  bucket_slots rounded up to a power of two.  Iceberg splits it as
+ *  nb_back = max(2, floor((17 nb + 50) / 100)) backyard buckets after
+ *  nb_front = nb - nb_back front-yard buckets; a key's front bucket is
+ *  floor(h1 nb_front / 2^64), its backyard buckets nb_front + floor(x nb_back /
+ *  2^32) for x = the high and the low 32 bits of h2 (the second moved to the
+ *  next backyard bucket, cyclically, when both coincide). */
 typedef struct {
   uint64_t capacity;
   int32_t scheme;        /* ws_scheme */
@@ -114,6 +127,7 @@ typedef struct {
   uint64_t seed1, seed2;  /* hash seeds of h1, h2 */
   uint64_t bytes;         /* device bytes owned (slots + tags + locks + counters) */
   int32_t scheme, metadata, device, never_erased;
+  uint64_t front_buckets; /* iceberg: front-yard buckets (the rest is the backyard); else nb */
 } ws_table_info;
 
 /* Create a table.  Slots start EMPTY.  Returns WS_ERR_OOM if device memory is
@@ -141,7 +155,17 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  calls whose keys are distinct and whose probed slots nothing else writes
  *  during the call (e.g. a pure query batch, or inserts of distinct new
  *  keys); otherwise results are undefined. */
-enum { WS_OPT_PRELOAD = 1, WS_OPT_PHASED = 2 };
+/*  WS_OPT_STREAM (default 1): single-table calls run "streaming lanes": each
+ *  warp serves a contiguous share of the batch, a lane follows its op's probe
+ *  sequence one bucket per wave and takes the next op as soon as its op
+ *  settles; ops the lanes cannot settle go to the tiles.  0 serves 32-op
+ *  chunks (lane waves, then tiles for what is left), as batched and serving
+ *  launches always do.
+ *  WS_OPT_LANE_WAVES (double hashing only; 0..255, 0 = default): buckets of a
+ *  probe sequence the lane path follows, one per wave, before an op still
+ *  open goes to the tiles.  Default: the whole sequence when streaming, 4 in
+ *  32-op chunks. */
+enum { WS_OPT_PRELOAD = 1, WS_OPT_PHASED = 2, WS_OPT_LANE_WAVES = 3, WS_OPT_STREAM = 4 };
 ws_status ws_set_option(ws_table* t, int option, int64_t value);
 
 /* Insert-if-unique (§5.1 Upsert with the empty callback).  status_out: per-op
@@ -199,7 +223,8 @@ ws_status ws_count(ws_table* t, uint64_t* out);
 ws_status ws_last_error(ws_table* t, uint64_t* n_full, uint64_t* n_timeout, uint64_t* n_badkey);
 
 /* Adversarial-benchmark hooks (§4.1): the bucket count, and each key's
- * primary bucket computed on the device (out: device or host u64[n]). */
+ * primary bucket b_0 -- for iceberg its front-yard bucket -- computed on the
+ * device (out: device or host u64[n]). */
 ws_status ws_num_buckets(const ws_table* t, uint64_t* out);
 ws_status ws_primary_bucket(ws_table* t, const uint64_t* keys, uint64_t* out, uint64_t n,
                             ws_stream stream);

@@ -75,6 +75,7 @@ def lib():
         L.ora_layout_check.restype = i32
         L.ora_candidates_full.argtypes = [vp, vp, u64, u64, i32, u64, u64, u64, vp, u64, vp]
         L.ora_primary_bucket.argtypes = [vp, u64, u64, u64, vp]
+        L.ora_iceberg_buckets.argtypes = [vp, u64, u64, u64, u64, vp]
         _lib = L
     return _lib
 
@@ -177,3 +178,19 @@ def primary_bucket(keys, nb, seed1):
     out = np.empty(k.size, np.uint64)
     lib().ora_primary_bucket(_p(k), k.size, nb, seed1, _p(out))
     return out
+
+
+def iceberg_buckets(keys, nb, seed1, seed2):
+    """(front, back_1, back_2) bucket of each key under the iceberg geometry."""
+    k = _u64(keys)
+    out = np.empty((k.size, 3), np.uint64)
+    lib().ora_iceberg_buckets(_p(k), k.size, nb, seed1, seed2, _p(out))
+    return out
+
+
+def primary_bucket_of(scheme, keys, nb, seed1, seed2):
+    """The bucket whose lock serialises inserters of a key: b_0, or the
+    front-yard bucket for iceberg."""
+    if scheme == 2:
+        return iceberg_buckets(keys, nb, seed1, seed2)[:, 0].copy()
+    return primary_bucket(keys, nb, seed1)

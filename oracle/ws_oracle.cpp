@@ -210,6 +210,16 @@ void ora_load(void* h, const uint64_t* keys, const uint64_t* vals, uint64_t n) {
 //   double hashing (§2.2):  b_i = (h1 + i*(h2|1)) mod nb,  i < P.
 //   two choice (§2.2):      b_0 = h1 mod nb, b_1 = h2 mod nb, and b_1 = b_0+1
 //                           mod nb when they coincide (nb > 1).
+//   iceberg (§2.2 front yard / backyard; 83% / 17% as listed in §5):
+//                           nb_back = max(2, floor((17 nb + 50) / 100)) buckets
+//                           follow nb_front = nb - nb_back front buckets;
+//                           front = floor(h1 nb_front / 2^64);
+//                           back_j = nb_front + floor(x_j nb_back / 2^32) with
+//                           x_1 = high 32 bits of h2, x_2 = low 32 bits; back_2
+//                           moves to the next backyard bucket (cyclic) when the
+//                           two coincide.  A key sits in the backyard only if
+//                           its front bucket was full when it was placed, so a
+//                           backyard key never has an EMPTY slot in its front.
 //   tag(k) = k & 0xffff, moved up by 2 when below 2 (0 = empty, 1 = tombstone),
 //   following §5 "Concurrency and metadata" (low 16 bits as the fingerprint).
 // ---------------------------------------------------------------------------
@@ -227,6 +237,24 @@ uint16_t spec_tag(uint64_t k) {
   uint16_t t = (uint16_t)(k & 0xffffu);
   return t < 2 ? (uint16_t)(t + 2) : t;
 }
+// Iceberg geometry: the three candidate buckets of a key (front, back_1, back_2).
+struct IcebergBuckets {
+  uint64_t front, back1, back2;
+};
+IcebergBuckets iceberg_buckets(uint64_t nb, uint64_t h1, uint64_t h2) {
+  uint64_t n_back = (17 * nb + 50) / 100;
+  if (n_back < 2) n_back = 2;
+  const uint64_t n_front = nb - n_back;
+  IcebergBuckets r;
+  r.front = (uint64_t)(((unsigned __int128)h1 * n_front) >> 64);
+  const uint64_t x1 = h2 >> 32, x2 = h2 & 0xffffffffull;
+  const uint64_t c1 = (x1 * n_back) >> 32;
+  uint64_t c2 = (x2 * n_back) >> 32;
+  if (c2 == c1) c2 = (c1 + 1) % n_back;
+  r.back1 = n_front + c1;
+  r.back2 = n_front + c2;
+  return r;
+}
 }  // namespace
 
 struct ora_layout_report {
@@ -238,7 +266,7 @@ struct ora_layout_report {
   uint64_t empty_not_suffix;  // an occupied slot after an empty one inside a bucket
 };
 
-// scheme: 0 double hashing, 1 two-choice.  tags may be null (no metadata).
+// scheme: 0 double hashing, 1 two-choice, 2 iceberg.  tags may be null (no metadata).
 int ora_layout_check(const uint64_t* slots /* 2*S words */, const uint16_t* tags, uint64_t nb,
                      uint64_t B, int scheme, uint64_t pmax, uint64_t seed1, uint64_t seed2,
                      ora_layout_report* r) {
@@ -298,6 +326,15 @@ int ora_layout_check(const uint64_t* slots /* 2*S words */, const uint16_t* tags
           }
           if (has_empty) { ++r->early_exit; break; }
         }
+      } else if (scheme == 2) {
+        const IcebergBuckets ib = iceberg_buckets(nb, h1, h2);
+        legal = (b == ib.front) || (b == ib.back1) || (b == ib.back2);
+        if (legal && b != ib.front) {
+          for (uint64_t q = 0; q < B; ++q) {
+            const uint64_t sq = ib.front * B + q;
+            if (tags ? tags[sq] == 0 : slots[2 * sq] == K_EMPTY) { ++r->early_exit; break; }
+          }
+        }
       } else {
         const uint64_t b0 = h1 & mask;
         uint64_t b1 = h2 & mask;
@@ -336,6 +373,9 @@ void ora_candidates_full(const uint64_t* slots, const uint16_t* tags, uint64_t n
     if (scheme == 0) {
       const uint64_t P = pmax < nb ? pmax : nb;
       for (uint64_t j = 0; j < P && all; ++j) all = bucket_full((h1 + j * (h2 | 1ull)) & mask);
+    } else if (scheme == 2) {
+      const IcebergBuckets ib = iceberg_buckets(nb, h1, h2);
+      all = bucket_full(ib.front) && bucket_full(ib.back1) && bucket_full(ib.back2);
     } else {
       const uint64_t b0 = h1 & mask;
       uint64_t b1 = h2 & mask;
@@ -351,6 +391,17 @@ void ora_candidates_full(const uint64_t* slots, const uint16_t* tags, uint64_t n
 void ora_primary_bucket(const uint64_t* keys, uint64_t n, uint64_t nb, uint64_t seed1,
                         uint64_t* out) {
   for (uint64_t i = 0; i < n; ++i) out[i] = fmix(keys[i] ^ seed1) & (nb - 1);
+}
+
+// Iceberg candidate buckets (front, back_1, back_2) of each key, 3 per key.
+void ora_iceberg_buckets(const uint64_t* keys, uint64_t n, uint64_t nb, uint64_t seed1, uint64_t seed2,
+                         uint64_t* out) {
+  for (uint64_t i = 0; i < n; ++i) {
+    const IcebergBuckets ib = iceberg_buckets(nb, fmix(keys[i] ^ seed1), fmix(keys[i] ^ seed2));
+    out[3 * i] = ib.front;
+    out[3 * i + 1] = ib.back1;
+    out[3 * i + 2] = ib.back2;
+  }
 }
 
 }  // extern "C"

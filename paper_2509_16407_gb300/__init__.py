@@ -19,7 +19,7 @@ __all__ = ["Table", "WsError", "SCHEMES", "UPSERT_OPS", "MISS", "FOUND", "INSERT
            "FAIL_BADKEY", "FAIL_TIMEOUT", "MX_QUERY", "MX_INSERT", "MX_ADD", "MX_MAX", "MX_REPLACE",
            "MX_ERASE", "lib", "BatchPlan", "BK_INSERT", "BK_UPSERT", "BK_QUERY", "BK_ERASE", "Server"]
 
-SCHEMES = {"double": 0, "p2": 1}
+SCHEMES = {"double": 0, "p2": 1, "iceberg": 2}
 UPSERT_OPS = {"add": 0, "max": 1, "replace": 2, "insert": 3}
 MISS, FOUND, INSERTED, FAIL_FULL, FAIL_BADKEY, FAIL_TIMEOUT = range(6)
 MX_QUERY, MX_INSERT, MX_ADD, MX_MAX, MX_REPLACE, MX_ERASE = range(6)
@@ -91,7 +91,8 @@ def _empty_like(x, n, kind):
 class Table:
     """A device-resident hash table (one GPU).
 
-    scheme: "double" (DoubleHT) or "p2" (P2HT); metadata: 16-bit fingerprints.
+    scheme: "double" (DoubleHT), "p2" (P2HT) or "iceberg" (IcebergHT, metadata
+    only); metadata: 16-bit fingerprints.
     bucket_slots / tile / max_probe / spin_limit: 0 selects the paper's default.
     """
 
@@ -150,6 +151,14 @@ class Table:
     def set_phased(self, on: bool):
         """Bulk-synchronous mode (weak cacheable loads, no locks; distinct keys only)."""
         _check(lib().ws_set_option(self._h, 2, int(bool(on))), "ws_set_option")
+
+    def set_lane_waves(self, n: int):
+        """Double hashing: buckets the lane path follows before the tiles (0 = default)."""
+        _check(lib().ws_set_option(self._h, 3, int(n)), "ws_set_option")
+
+    def set_stream(self, on: bool):
+        """Streaming lanes in single-table calls (on by default) or 32-op chunks."""
+        _check(lib().ws_set_option(self._h, 4, int(bool(on))), "ws_set_option")
 
     def clear(self, stream=None):
         _check(lib().ws_clear(self._h, self._stream(stream)), "ws_clear")

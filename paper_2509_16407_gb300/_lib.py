@@ -25,7 +25,8 @@ class WsInfo(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_uint64), ("buckets", ctypes.c_uint64), ("bucket_slots", ctypes.c_uint64),
                 ("tile", ctypes.c_uint64), ("max_probe", ctypes.c_uint64), ("seed1", ctypes.c_uint64),
                 ("seed2", ctypes.c_uint64), ("bytes", ctypes.c_uint64), ("scheme", ctypes.c_int32),
-                ("metadata", ctypes.c_int32), ("device", ctypes.c_int32), ("never_erased", ctypes.c_int32)]
+                ("metadata", ctypes.c_int32), ("device", ctypes.c_int32), ("never_erased", ctypes.c_int32),
+                ("front_buckets", ctypes.c_uint64)]
 
 
 class WsBatchItem(ctypes.Structure):

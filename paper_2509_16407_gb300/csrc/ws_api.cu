@@ -122,6 +122,7 @@ cudaError_t wsi::dispatch(const ws_table* t, const ws::TableView& tv, const ws::
   if (t->scheme == WS_DOUBLE)
     return t->meta ? ws::launch_double_meta(B, T, tv, a, kind, s, t->num_sms)
                    : ws::launch_double_plain(B, T, tv, a, kind, s, t->num_sms);
+  if (t->scheme == WS_ICEBERG) return ws::launch_iceberg_meta(B, T, tv, a, kind, s, t->num_sms);
   return t->meta ? ws::launch_p2_meta(B, T, tv, a, kind, s, t->num_sms)
                  : ws::launch_p2_plain(B, T, tv, a, kind, s, t->num_sms);
 }
@@ -206,9 +207,13 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
   return WS_OK;
 }
 
-__global__ void primary_bucket_kernel(const u64* keys, u64* out, u64 n, u64 seed1, u64 mask) {
-  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
-    out[i] = ws::fmix64(keys[i] ^ seed1) & mask;
+// b_0 of each key (iceberg: the front-yard bucket, whose lock inserters take).
+__global__ void primary_bucket_kernel(const u64* keys, u64* out, u64 n, u64 seed1, u64 mask, u64 nb_front,
+                                      int iceberg) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    const u64 h1 = ws::fmix64(keys[i] ^ seed1);
+    out[i] = iceberg ? __umul64hi(h1, nb_front) : (h1 & mask);
+  }
 }
 
 }  // namespace
@@ -219,7 +224,8 @@ __global__ void primary_bucket_kernel(const u64* keys, u64* out, u64 n, u64 seed
 ws_status wsi::table_create(const ws_config* cfg, cudaStream_t stream, ws_table** out) {
   if (!cfg || !out) return WS_ERR_INVALID;
   *out = nullptr;
-  if (cfg->scheme != WS_DOUBLE && cfg->scheme != WS_P2) return WS_ERR_INVALID;
+  if (cfg->scheme != WS_DOUBLE && cfg->scheme != WS_P2 && cfg->scheme != WS_ICEBERG) return WS_ERR_INVALID;
+  if (cfg->scheme == WS_ICEBERG && !cfg->metadata) return WS_ERR_INVALID;  // IcebergHT(M) only
   if (cfg->capacity == 0 || cfg->capacity > (1ull << 40)) return WS_ERR_INVALID;
   const int meta = cfg->metadata ? 1 : 0;
   int B = cfg->bucket_slots ? cfg->bucket_slots : ((cfg->scheme == WS_DOUBLE && !meta) ? 8 : 32);
@@ -239,6 +245,7 @@ ws_status wsi::table_create(const ws_config* cfg, cudaStream_t stream, ws_table*
   u64 nb = 1;
   const u64 want = (cfg->capacity + (u64)B - 1) / (u64)B;
   while (nb < want) nb <<= 1;
+  if (cfg->scheme == WS_ICEBERG && nb < 4) nb = 4;  // a front yard and a two-bucket backyard
   t->nb = nb;
   t->B = (u64)B;
   t->S = nb * (u64)B;
@@ -274,12 +281,21 @@ ws_status wsi::table_create(const ws_config* cfg, cudaStream_t stream, ws_table*
   }
   t->bytes = t->S * sizeof(ws::Slot) + (meta ? t->S * 2 : 0) + lock_words * 4 + sizeof(ws::Counters);
   tv.nb_mask = nb - 1;
+  tv.nb_front = nb;
+  tv.nb_back = 0;
+  if (cfg->scheme == WS_ICEBERG) {
+    // backyard = 17% of the buckets, rounded to nearest, at least 2 (§5)
+    tv.nb_back = (17 * nb + 50) / 100;
+    if (tv.nb_back < 2) tv.nb_back = 2;
+    tv.nb_front = nb - tv.nb_back;
+  }
   tv.seed1 = kSeed1;
   tv.seed2 = kSeed2;
   tv.pmax = t->pmax;
   tv.spin_limit = t->spin;
   tv.shortcut = 1;
   tv.preload = kDefaultPreload;
+  tv.stream = 1;  // streaming lanes in single-table launches (see WS_OPT_STREAM)
   auto clear = [&](void* p, size_t bytes) {
     return stream ? cudaMemsetAsync(p, 0, bytes, stream) : cudaMemset(p, 0, bytes);
   };
@@ -370,7 +386,7 @@ ws_status ws_table_info_get(const ws_table* t, ws_table_info* o) {
   o->buckets = t->nb;
   o->bucket_slots = t->B;
   o->tile = (u64)t->T;
-  o->max_probe = t->scheme == WS_DOUBLE ? t->pmax : (t->nb > 1 ? 2 : 1);
+  o->max_probe = t->scheme == WS_DOUBLE ? t->pmax : t->scheme == WS_ICEBERG ? 3 : (t->nb > 1 ? 2 : 1);
   o->seed1 = t->tv.seed1;
   o->seed2 = t->tv.seed2;
   o->bytes = t->bytes;
@@ -378,6 +394,7 @@ ws_status ws_table_info_get(const ws_table* t, ws_table_info* o) {
   o->metadata = t->meta;
   o->device = t->device;
   o->never_erased = t->never_erased;
+  o->front_buckets = t->tv.nb_front;
   return WS_OK;
 }
 
@@ -410,6 +427,14 @@ ws_status ws_set_option(ws_table* t, int option, int64_t value) {
     case WS_OPT_PHASED:
       if (value != 0 && value != 1) return WS_ERR_INVALID;
       t->tv.phased = (int)value;
+      return WS_OK;
+    case WS_OPT_LANE_WAVES:
+      if (value < 0 || value > 255) return WS_ERR_INVALID;
+      t->tv.lane_waves = (int)value;
+      return WS_OK;
+    case WS_OPT_STREAM:
+      if (value != 0 && value != 1) return WS_ERR_INVALID;
+      t->tv.stream = (int)value;
       return WS_OK;
   }
   return WS_ERR_INVALID;
@@ -514,7 +539,8 @@ ws_status ws_primary_bucket(ws_table* t, const uint64_t* keys, uint64_t* out, ui
   }
   if (po == PTR_HOST) WS_CUDA(cudaMallocAsync(&dout, n * 8, s));
   const unsigned grid = (unsigned)((n + 255) / 256 < 65535 ? (n + 255) / 256 : 65535);
-  primary_bucket_kernel<<<grid, 256, 0, s>>>(dk, dout, n, t->tv.seed1, t->tv.nb_mask);
+  primary_bucket_kernel<<<grid, 256, 0, s>>>(dk, dout, n, t->tv.seed1, t->tv.nb_mask, t->tv.nb_front,
+                                             t->scheme == WS_ICEBERG ? 1 : 0);
   WS_CUDA(cudaGetLastError());
   if (po == PTR_HOST) {
     WS_CUDA(cudaMemcpyAsync(out, dout, n * 8, cudaMemcpyDeviceToHost, s));

@@ -31,7 +31,7 @@ enum { ST_MISS = 0, ST_FOUND = 1, ST_INSERTED = 2, ST_FULL = 3, ST_BADKEY = 4, S
 enum { OP_ADD = 0, OP_MAX = 1, OP_REPLACE = 2, OP_INSERT = 3 };
 enum { MX_QUERY = 0, MX_INSERT = 1, MX_ADD = 2, MX_MAX = 3, MX_REPLACE = 4, MX_ERASE = 5 };
 enum { KIND_QUERY = 0, KIND_UPSERT = 1, KIND_ERASE = 2, KIND_MIXED = 3, KIND_PROBE = 4 };
-enum { SCHEME_DOUBLE = 0, SCHEME_P2 = 1 };
+enum { SCHEME_DOUBLE = 0, SCHEME_P2 = 1, SCHEME_ICEBERG = 2 };
 
 struct __align__(16) Slot {
   u64 key, val;
@@ -53,12 +53,16 @@ struct TableView {
   u32* locks;     // one bit per bucket
   Counters* ctr;
   u64 nb_mask;    // nb - 1
+  u64 nb_front;   // iceberg: front-yard buckets [0, nb_front), backyard [nb_front, nb)
+  u64 nb_back;    // iceberg: nb - nb_front (at least 2)
   u64 seed1, seed2;
   u32 pmax;       // double hashing: buckets a probe sequence may visit (<= nb)
   u32 spin_limit; // lock attempts before giving up
   int shortcut;   // P2: no erase ever ran, so the primary-fill shortcut is exact
   int preload;    // stage each op's first probe into shared memory with async copies (1) or not (0)
   int phased;     // bulk-synchronous mode: weak cacheable probe loads, no locks (see WS_OPT_PHASED)
+  int lane_waves; // double hashing: buckets the lane path checks before the tiles (0 = default)
+  int stream;     // single-table launches: streaming lanes (1) or 32-op chunks (0); see WS_OPT_STREAM
 };
 
 struct BatchArgs {
@@ -113,11 +117,15 @@ __device__ __forceinline__ void ld_slot(const Slot* p, u64& k, u64& v) {
       : "memory");
 }
 
-__device__ __forceinline__ void st_slot_release(Slot* p, u64 k, u64 v) {
+// The pair store of a metadata claim.  It follows the tag CAS, which has
+// acquire semantics, so it cannot be performed before the claim; no earlier
+// write of the thread needs to be published with it, so no release (a
+// release store waits for all of them).
+__device__ __forceinline__ void st_slot_relaxed(Slot* p, u64 k, u64 v) {
   asm volatile(
       "{\n\t.reg .b128 t;\n\t"
       "mov.b128 t, {%1, %2};\n\t"
-      "st.release.gpu.global.b128 [%0], t;\n\t}" ::"l"(p),
+      "st.relaxed.gpu.global.b128 [%0], t;\n\t}" ::"l"(p),
       "l"(k), "l"(v)
       : "memory");
 }

@@ -107,6 +107,7 @@ struct TileOps {
   static_assert(B == 8 || B == 16 || B == 32, "bucket size");
   static_assert(T == 4 || T == 8 || T == 16 || T == 32, "tile size");
   static_assert(!META || B == 32, "metadata tables use 32-slot buckets (one 64-byte tag line)");
+  static_assert(SCHEME != SCHEME_ICEBERG || META, "the iceberg scheme is built with metadata only");
   static constexpr int G = (T > B) ? (T / B) : 1;    // buckets covered by one step
   static constexpr int LPB = (T > B) ? B : T;        // lanes per bucket in a step
   static constexpr int SPB = (T > B) ? 1 : (B / T);  // steps per bucket
@@ -128,11 +129,24 @@ struct TileOps {
 
   __device__ static __forceinline__ u32 nprobe(const TableView& tv) {
     if (SCHEME == SCHEME_DOUBLE) return tv.pmax;
+    if (SCHEME == SCHEME_ICEBERG) return 3u;
     return tv.nb_mask == 0 ? 1u : 2u;
   }
 
+  // Candidate bucket i of a key.  Iceberg (§2.2 front yard / backyard): i = 0
+  // is the front-yard bucket by single hashing, i = 1, 2 the two backyard
+  // choices; bucket counts are not powers of two there, so indices come from
+  // multiply-high range reduction (h * n / 2^64, resp. / 2^32 on 32-bit halves).
   __device__ static __forceinline__ u64 bucket(const TableView& tv, u64 h1, u64 h2, u32 i) {
     if (SCHEME == SCHEME_DOUBLE) return (h1 + (u64)i * (h2 | 1ull)) & tv.nb_mask;
+    if (SCHEME == SCHEME_ICEBERG) {
+      if (i == 0) return __umul64hi(h1, tv.nb_front);
+      const u64 c1 = ((h2 >> 32) * tv.nb_back) >> 32;
+      if (i == 1) return tv.nb_front + c1;
+      u64 c2 = ((h2 & 0xffffffffull) * tv.nb_back) >> 32;
+      if (c2 == c1) c2 = (c1 + 1 == tv.nb_back) ? 0 : c1 + 1;
+      return tv.nb_front + c2;
+    }
     const u64 b0 = h1 & tv.nb_mask;
     if (i == 0) return b0;
     u64 b1 = h2 & tv.nb_mask;
@@ -481,6 +495,8 @@ struct TileOps {
       if (got) return {true, idx, val};
       if (SCHEME == SCHEME_DOUBLE) {
         if (me) break;
+      } else if (SCHEME == SCHEME_ICEBERG) {
+        if (i == 0 && me) break;  // a front bucket with an EMPTY slot never overflowed
       } else if (i == 0 && tv.shortcut && (u32)(32 - __popc(mf)) < FILL_SHORTCUT) {
         break;
       }
@@ -516,6 +532,51 @@ struct TileOps {
           r.fk = ((me >> q) & 1u) ? TAG_EMPTY : TAG_TOMB;
         }
         if (me) return r;
+      }
+      return r;
+    }
+    if (SCHEME == SCHEME_ICEBERG) {
+      // Front bucket first; its first free slot (EMPTY or TOMB) wins.  A
+      // front bucket holding an EMPTY slot was never full, so the key cannot
+      // be in the backyard.  Otherwise both backyard buckets are searched and,
+      // with no free front slot, the key goes to the less loaded one (ties to
+      // the first), or to the other one when that is full.
+      u32 occ[3] = {0, 0, 0};
+      bool hf[3] = {false, false, false};
+      u64 fi[3] = {0, 0, 0}, ft[3] = {0, 0, 0};
+      u32 nread = 0;
+      for (u32 bi = 0; bi < 3; ++bi) {
+        const u64 b = bucket(tv, h1, h2, bi);
+        const PreRef p = (bi == 0) ? pre : no_pre();
+        unsigned mm, me, mf;
+        tag_masks(tv, c, b, kt, p, mm, me, mf);
+        if (verify<WAIT>(tv, c, b, mm, K, p, r.idx, r.val, &r.stuck)) {
+          r.found = true;
+          return r;
+        }
+        if (r.stuck) return r;
+        occ[bi] = (u32)(32 - __popc(mf));
+        if (mf) {
+          const int q = __ffs(mf) - 1;
+          hf[bi] = true;
+          fi[bi] = b * 32 + (u64)q;
+          ft[bi] = ((me >> q) & 1u) ? TAG_EMPTY : TAG_TOMB;
+        }
+        nread = bi + 1;
+        if (bi == 0 && me) break;
+      }
+      int ch = -1;
+      if (hf[0]) {
+        ch = 0;
+      } else if (nread == 3) {
+        ch = (occ[2] < occ[1]) ? 2 : 1;
+        if (!hf[ch]) ch = 3 - ch;
+        if (!hf[ch]) ch = -1;
+      }
+      if (ch >= 0) {
+        r.has_free = true;
+        r.fidx = fi[ch];
+        r.fk = ft[ch];
       }
       return r;
     }
@@ -563,14 +624,14 @@ struct TileOps {
   // ----------------------------------------------------------------------
   __device__ static __forceinline__ Hit find(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
                                              PreRef pre) {
-    if (META) return find_meta(tv, c, K, h1, h2, pre);
-    return find_plain(tv, c, K, h1, h2, pre);
+    if constexpr (META) return find_meta(tv, c, K, h1, h2, pre);
+    else return find_plain(tv, c, K, h1, h2, pre);
   }
   template <bool WAIT = false>
   __device__ static __forceinline__ Scan scan(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2,
                                               PreRef pre) {
-    if (META) return scan_meta<WAIT>(tv, c, K, h1, h2, pre);
-    return scan_plain(tv, c, K, h1, h2, pre);
+    if constexpr (META) return scan_meta<WAIT>(tv, c, K, h1, h2, pre);
+    else return scan_plain(tv, c, K, h1, h2, pre);
   }
 
   // Claim the scanned free slot for (K, V).  Leader lane writes; all learn the outcome.
@@ -581,7 +642,7 @@ struct TileOps {
       if (META) {
         const u16 expect = (u16)r.fk;
         if (ptx::cas_tag(tv.tags + r.fidx, expect, key_tag(K)) == expect) {
-          ptx::st_slot_release(tv.slots + r.fidx, K, V);
+          ptx::st_slot_relaxed(tv.slots + r.fidx, K, V);
           ok = 1;
         }
       } else {
@@ -675,7 +736,7 @@ struct TileOps {
     const u64 h1 = fmix64(K ^ tv.seed1), h2 = fmix64(K ^ tv.seed2);
     u32 sec = 0, lin = 0;
     Hit h;
-    if (META)
+    if constexpr (META)
       h = find_meta<true>(tv, c, K, h1, h2, no_pre(), &sec, &lin);
     else
       h = find_plain<true>(tv, c, K, h1, h2, no_pre(), &sec, &lin);
@@ -889,6 +950,9 @@ struct TileOps {
     bool ff_set;  // first free slot of the probe sequence seen so far
     u64 ff_idx, ff_k, ff_v;
     u32 occ0;     // two-choice: load of b_0 (wave 0)
+    u32 occ1;     // iceberg: load and first free tag of the first backyard bucket (wave 1)
+    bool f1_set;
+    u64 f1_idx, f1_k;
   };
 
   __device__ static __forceinline__ int lane_wave(const TableView& tv, PreRef p, u64 K, u64 V, int op, int opk,
@@ -925,6 +989,12 @@ struct TileOps {
     if (!META && PRE_SLOTS < B && !sn.empty) return -1;
     const bool ins = (opk == LW_INSERT_FREE || opk == LW_INSERT_LOCKED);
     if (SCHEME == SCHEME_P2 && w == 0) ls.occ0 = sn.occ;
+    if (SCHEME == SCHEME_ICEBERG && w == 1) {
+      ls.occ1 = sn.occ;
+      ls.f1_set = sn.ffree >= 0;
+      ls.f1_idx = bw * 32 + (u64)(sn.ffree >= 0 ? sn.ffree : 0);
+      ls.f1_k = sn.ffree_empty ? TAG_EMPTY : TAG_TOMB;
+    }
     if (ins && !ls.ff_set && sn.ffree >= 0 && (SCHEME == SCHEME_DOUBLE || w == 0)) {
       ls.ff_set = true;
       if (META) {
@@ -941,6 +1011,8 @@ struct TileOps {
     bool ends;
     if (SCHEME == SCHEME_DOUBLE)
       ends = sn.empty || w + 1 >= P;
+    else if (SCHEME == SCHEME_ICEBERG)
+      ends = (w == 0 && sn.empty) || w + 1 >= P;
     else
       ends = (w + 1 >= P) || (w == 0 && tv.shortcut && sn.occ < FILL_SHORTCUT);
     if (!ends) return 0;
@@ -954,6 +1026,26 @@ struct TileOps {
     u64 fidx = ls.ff_idx, fk = ls.ff_k, fv = ls.ff_v;
     if (SCHEME == SCHEME_DOUBLE) {
       if (!sn.empty || !ls.ff_set) return -1;
+    } else if (SCHEME == SCHEME_ICEBERG) {
+      // a free front slot (recorded in wave 0) wins; else the backyard choice
+      // between wave 1's bucket and this one (wave 2), ties to the first
+      if (!ls.ff_set) {
+        const bool free2 = sn.ffree >= 0;
+        int ch = (sn.occ < ls.occ1) ? 2 : 1;
+        if (ch == 2 && !free2) ch = 1;
+        else if (ch == 1 && !ls.f1_set) ch = 2;
+        if (ch == 2 ? !free2 : !ls.f1_set) {
+          st = ST_FULL;
+          return 1;
+        }
+        if (ch == 1) {
+          fidx = ls.f1_idx;
+          fk = ls.f1_k;
+        } else {
+          fidx = bw * 32 + (u64)sn.ffree;
+          fk = sn.ffree_empty ? TAG_EMPTY : TAG_TOMB;
+        }
+      }
     } else {
       // K is absent from its buckets and the lane holds b_0's lock: place it
       const bool free0 = (w == 0) ? sn.ffree >= 0 : ls.ff_set;
@@ -978,7 +1070,7 @@ struct TileOps {
     if (META) {
       const u16 expect = (u16)fk;
       ok = ptx::cas_tag(tv.tags + fidx, expect, key_tag(K)) == expect;
-      if (ok) ptx::st_slot_release(tv.slots + fidx, K, V);
+      if (ok) ptx::st_slot_relaxed(tv.slots + fidx, K, V);
     } else {
       ok = ptx::cas_slot(tv.slots + fidx, fk, fv, K, V);
     }
@@ -1211,9 +1303,16 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
   typename Ops::LaneState ls;
   ls.ff_set = false;
   ls.ff_idx = ls.ff_k = ls.ff_v = 0;
-  ls.occ0 = 0;
-  constexpr u32 kMaxWaves = kRounds ? 0u : (SCHEME == SCHEME_DOUBLE) ? 4u : 2u;
-  for (u32 w = 0; w < kMaxWaves; ++w) {
+  ls.occ0 = ls.occ1 = 0;
+  ls.f1_set = false;
+  ls.f1_idx = ls.f1_k = 0;
+  // waves: a double-hashing sequence is followed for lane_waves buckets
+  // (default 4); the other schemes have 2 or 3 candidate buckets
+  const u32 max_waves = kRounds                    ? 0u
+                        : (SCHEME == SCHEME_DOUBLE) ? (tv.lane_waves > 0 ? (u32)tv.lane_waves : 4u)
+                        : (SCHEME == SCHEME_ICEBERG) ? 3u
+                                                     : 2u;
+  for (u32 w = 0; w < max_waves; ++w) {
     const bool want = lane_ok && !done;
     const unsigned wmask = __ballot_sync(0xffffffffu, want);
     if (!wmask) break;
@@ -1308,6 +1407,198 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
   return dcount + tile_d;
 }
 
+// -------------------------------------------------------------------------
+// Streaming lanes: one warp serves a contiguous range of ops.  Each lane holds
+// one op at a time and follows its probe sequence wave by wave (one bucket per
+// wave, copied with cp.async like the chunk path); a lane whose op settles
+// takes the next op of the range before the next wave, so every wave keeps
+// up to 32 probes in flight however long the individual sequences are.  Ops
+// the lane path cannot settle (a lost CAS, an unsure tag match, an insert
+// without the lock, the probe-count kernel) are parked and served by the
+// cooperative tiles, which run only when no lane of the warp is active -- so
+// no lane of the warp holds a bucket lock a tile might wait for.  Refill
+// pauses once enough ops are parked to fill the tiles.
+// -------------------------------------------------------------------------
+template <int SCHEME, bool META, int B, int T, int KIND>
+__device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs& a, int upsert_op, bool lockfree,
+                                           u64 begin, u64 end, WarpSmem& sm, int lane) {
+  using Ops = TileOps<SCHEME, META, B, T>;
+  enum { L_EMPTY = 0, L_ACTIVE = 1, L_PARKED = 2 };
+  constexpr int NT = 32 / T;
+  constexpr unsigned kAll = 0xffffffffu;
+  constexpr bool kLaneLock = (SCHEME == SCHEME_DOUBLE) || META || Ops::PRE_SLOTS == B;
+  const u64 ks = a.key_stride ? a.key_stride : 1;
+  const bool lane_path = (KIND != KIND_PROBE) && tv.preload;
+  // a cap on the waves of one op (WS_OPT_LANE_WAVES); by default the whole sequence
+  const u32 cap = (SCHEME == SCHEME_DOUBLE && tv.lane_waves > 0) ? (u32)tv.lane_waves : 0xffffffffu;
+  // a lane's op (key, value, hashes, index) lives in its shared-memory
+  // columns; registers hold only the probe state
+  int state = L_EMPTY;
+  int opk = -1, op = upsert_op;
+  bool locked = false, fresh = true;
+  u32 w = 0;
+  typename Ops::LaneState ls;
+  int dcount = 0, tile_d = 0;
+  u64 next = begin;
+  for (;;) {
+    // 1. refill: empty lanes take the next ops of the range, in lane order
+    unsigned parked = __ballot_sync(kAll, state == L_PARKED);
+    const unsigned empty = __ballot_sync(kAll, state == L_EMPTY);
+    if (empty && next < end && __popc(parked) < NT) {
+      const u64 rank = (u64)__popc(empty & ((1u << lane) - 1u));
+      if (state == L_EMPTY && next + rank < end) {
+        const u64 gi = next + rank;
+        const u64 K = a.keys[gi * ks];
+        const u64 V = ((KIND == KIND_UPSERT || KIND == KIND_MIXED) && a.vals) ? a.vals[gi * ks] : 0;
+        const u8 code = (KIND == KIND_MIXED) ? a.ops[gi] : 0;
+        const u64 h1 = fmix64(K ^ tv.seed1), h2 = fmix64(K ^ tv.seed2);
+        u8 st = ST_MISS;
+        bool settled = false;
+        op = upsert_op;
+        opk = -1;
+        if (KIND == KIND_UPSERT && (a.flags & BATCH_SKIP_SENTINELS) && is_sentinel(K)) {
+          settled = true;  // an empty / erased slot of a rehash source: MISS
+          if (a.vals_out) a.vals_out[gi] = 0;
+          if (a.status_out) a.status_out[gi] = ST_MISS;
+        } else if (is_sentinel(K) || (KIND == KIND_MIXED && code > MX_ERASE)) {
+          settled = true;
+          st = ST_BADKEY;
+          count_failure(tv, st);
+          if (a.vals_out) a.vals_out[gi] = 0;
+          if (a.status_out) a.status_out[gi] = st;
+        } else {
+          int kind = KIND;
+          if (KIND == KIND_MIXED) {
+            kind = code == MX_QUERY ? KIND_QUERY : code == MX_ERASE ? KIND_ERASE : KIND_UPSERT;
+            op = code == MX_INSERT ? OP_INSERT : code == MX_ADD ? OP_ADD : code == MX_MAX ? OP_MAX : OP_REPLACE;
+          }
+          opk = kind == KIND_QUERY ? Ops::LW_QUERY
+                : kind == KIND_ERASE ? Ops::LW_ERASE
+                : (KIND == KIND_UPSERT && lockfree && SCHEME == SCHEME_DOUBLE) ? Ops::LW_INSERT_FREE
+                                                                                 : Ops::LW_UPDATE_ONLY;
+        }
+        if (!settled) {
+          sm.key[lane] = K;
+          sm.val[lane] = V;
+          sm.op[lane] = code;
+          sm.h1[lane] = h1;
+          sm.h2[lane] = h2;
+          sm.out[lane] = gi;  // the op's index
+          w = 0;
+          fresh = true;
+          ls.ff_set = false;
+          ls.ff_idx = ls.ff_k = ls.ff_v = 0;
+          ls.occ0 = ls.occ1 = 0;
+          ls.f1_set = false;
+          ls.f1_idx = ls.f1_k = 0;
+          locked = false;
+          if (!lane_path) {
+            state = L_PARKED;
+          } else {
+            if (kLaneLock && opk == Ops::LW_UPDATE_ONLY) {
+              locked = tv.phased || Ops::lane_lock(tv, Ops::bucket(tv, h1, h2, 0));
+              if (locked) opk = Ops::LW_INSERT_LOCKED;
+            }
+            state = L_ACTIVE;
+          }
+        }
+      }
+      const u64 took = (u64)__popc(empty);
+      next = (end - next < took) ? end : next + took;
+    }
+    // 2. one wave: copy each active lane's current bucket, then settle
+    const unsigned act = __ballot_sync(kAll, state == L_ACTIVE);
+    if (act) {
+      sm.bw[lane] = (state == L_ACTIVE) ? Ops::bucket(tv, sm.h1[lane], sm.h2[lane], w) : 0;
+      __syncwarp();
+      if (META) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int j = i * 8 + (lane >> 2), part = lane & 3;
+          if ((act >> j) & 1u) ptx::cp_async16(&sm.pre.line[part][j], tv.tags + sm.bw[j] * 32 + 8 * part);
+        }
+      } else {
+        constexpr int PS = Ops::PRE_SLOTS;
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+          const int j = i * (32 / PS) + lane / PS, part = lane % PS;
+          if ((act >> j) & 1u) ptx::cp_async16(&sm.pre.line[part][j], tv.slots + sm.bw[j] * B + (u64)part);
+        }
+      }
+      ptx::cp_async_wait_all();
+      __syncwarp();
+      if (META) {
+        if (state == L_ACTIVE) Ops::preload_candidate(tv, sm.key[lane], sm.bw[lane], &sm.pre, lane);
+        ptx::cp_async_wait_all();
+        __syncwarp();
+      }
+      if (state == L_ACTIVE) {
+        const PreRef p{&sm.pre, lane};
+        u64 out = 0;
+        u8 st = ST_MISS;
+        const int r =
+            Ops::lane_wave(tv, p, sm.key[lane], sm.val[lane], op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh);
+        if (r > 0) {
+          const u64 gi = sm.out[lane];
+          if (a.vals_out) a.vals_out[gi] = out;
+          if (a.status_out) a.status_out[gi] = st;
+          if (st >= ST_FULL) count_failure(tv, st);
+          state = L_EMPTY;
+        } else if (r < 0 || w + 1 >= cap) {
+          state = L_PARKED;
+        } else {
+          ++w;
+        }
+        if (state != L_ACTIVE && locked) {
+          if (!tv.phased) Ops::lane_unlock(tv, Ops::bucket(tv, sm.h1[lane], sm.h2[lane], 0));  // after the claim
+          locked = false;
+        }
+      }
+      __syncwarp();  // the next wave overwrites the snapshots
+    }
+    // 3. tiles: parked ops, once no lane is active (no lane holds a lock)
+    const bool any_active = __any_sync(kAll, state == L_ACTIVE);
+    parked = __ballot_sync(kAll, state == L_PARKED);
+    if (parked && !any_active) {
+      const TileCtx<T> c = make_tile<T>(lane);
+      const int tile = lane / T;
+      const int n_todo = __popc(parked);
+      for (int k = 0; k * NT < n_todo; ++k) {
+        const int rank = k * NT + tile;
+        if (rank >= n_todo) continue;  // tile-uniform
+        const int j = (int)__fns(parked, 0, rank + 1);
+        const u64 Kj = sm.key[j], h1j = sm.h1[j], h2j = sm.h2[j], gj = sm.out[j];
+        u64 o = 0;
+        u8 sj;
+        int rd = 0;
+        if (KIND == KIND_QUERY) {
+          sj = Ops::do_query(tv, c, Kj, h1j, h2j, no_pre(), o);
+        } else if (KIND == KIND_PROBE) {
+          sj = Ops::do_probe(tv, c, Kj, o);
+        } else if (KIND == KIND_UPSERT) {
+          sj = lockfree ? Ops::template do_upsert<true>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, no_pre(), rd)
+                        : Ops::template do_upsert<false>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, no_pre(), rd);
+        } else if (KIND == KIND_ERASE) {
+          sj = Ops::do_erase(tv, c, Kj, h1j, h2j, no_pre(), o, rd);
+        } else {
+          sj = Ops::do_mixed(tv, c, sm.op[j], Kj, h1j, h2j, sm.val[j], no_pre(), o, rd);
+        }
+        if (c.tl == 0) {
+          if (a.vals_out) a.vals_out[gj] = o;
+          if (a.status_out) a.status_out[gj] = sj;
+          count_failure(tv, sj);
+          tile_d += rd;
+        }
+      }
+      __syncwarp();
+      if (state == L_PARKED) state = L_EMPTY;
+    } else if (!any_active && next >= end) {
+      break;  // nothing active, parked or left to take
+    }
+  }
+  return dcount + tile_d;
+}
+
 template <int SCHEME, bool META, int B, int T, int KIND>
 __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchArgs a) {
   __shared__ WarpSmem s_w[kWarps];
@@ -1317,10 +1608,23 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
   __syncthreads();
   const bool lockfree = (KIND == KIND_UPSERT);  // one call is one phase: no erase runs with it
   int dcount = 0;
-  const u64 nchunks = (a.n + 31) / 32;
-  const u64 stride = (u64)gridDim.x * kWarps;
-  for (u64 ch = (u64)blockIdx.x * kWarps + w; ch < nchunks; ch += stride)
-    dcount += warp_chunk<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, ch * 32, s_w[w], lane);
+  constexpr bool kRounds = (SCHEME == SCHEME_P2) && !META && B == 32;
+  if (kRounds || !tv.stream) {
+    // 32-op chunks, grid-stride
+    const u64 nchunks = (a.n + 31) / 32;
+    const u64 stride = (u64)gridDim.x * kWarps;
+    for (u64 ch = (u64)blockIdx.x * kWarps + w; ch < nchunks; ch += stride)
+      dcount += warp_chunk<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, ch * 32, s_w[w], lane);
+  } else {
+    // streaming lanes: each warp takes an equal contiguous share of the batch
+    const u64 warps = (u64)gridDim.x * kWarps;
+    const u64 per = ((a.n + warps - 1) / warps + 31) / 32 * 32;
+    const u64 begin = ((u64)blockIdx.x * kWarps + w) * per;
+    if (begin < a.n) {
+      const u64 end = (a.n - begin < per) ? a.n : begin + per;
+      dcount += warp_stream<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, begin, end, s_w[w], lane);
+    }
+  }
   if (KIND != KIND_QUERY && KIND != KIND_PROBE) {
     const int mine = __reduce_add_sync(0xffffffffu, dcount);
     if (lane == 0 && mine) atomicAdd((unsigned long long*)&s_cnt, (unsigned long long)(long long)mine);
@@ -1365,5 +1669,6 @@ cudaError_t launch_double_plain(int B, int T, const TableView&, const BatchArgs&
 cudaError_t launch_double_meta(int B, int T, const TableView&, const BatchArgs&, int kind, cudaStream_t, int);
 cudaError_t launch_p2_plain(int B, int T, const TableView&, const BatchArgs&, int kind, cudaStream_t, int);
 cudaError_t launch_p2_meta(int B, int T, const TableView&, const BatchArgs&, int kind, cudaStream_t, int);
+cudaError_t launch_iceberg_meta(int B, int T, const TableView&, const BatchArgs&, int kind, cudaStream_t, int);
 
 }  // namespace ws

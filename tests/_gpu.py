@@ -2,8 +2,8 @@
 parameters.  No method arithmetic here."""
 import numpy as np
 
-DESIGNS = [("double", False), ("double", True), ("p2", False), ("p2", True)]
-DESIGN_IDS = ["DoubleHT", "DoubleHT(M)", "P2HT", "P2HT(M)"]
+DESIGNS = [("double", False), ("double", True), ("p2", False), ("p2", True), ("iceberg", True)]
+DESIGN_IDS = ["DoubleHT", "DoubleHT(M)", "P2HT", "P2HT(M)", "IcebergHT(M)"]
 
 
 def dev(a, device="cuda"):

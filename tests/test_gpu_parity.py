@@ -60,8 +60,9 @@ def test_golden_adversarial_fig2_single(ws, oracle_mod, scheme, meta):
     t = ws.Table(1 << 10, scheme, meta)
     nb = t.num_buckets()
     cand = W.distinct_keys(77, 4096)
+    inf = t.info()
     pb = host(t.primary_bucket(dev(cand)))
-    assert (pb == oracle_mod.primary_bucket(cand, nb, t.info()["seed1"])).all()
+    assert (pb == oracle_mod.primary_bucket_of(inf["scheme"], cand, nb, inf["seed1"], inf["seed2"])).all()
     b = pb[0]
     X, Y = cand[0], cand[1:][pb[1:] == b][0]
     t.insert(dev(np.array([X], np.uint64)), dev(np.array([100], np.uint64)))
@@ -137,7 +138,8 @@ def test_config2_small(ws, oracle_mod, scheme, meta, tile, load):
     full = st == ws.FAIL_FULL
     # two-choice placement depends on the interleaving: at 0.9 the sequential
     # order already fills some buckets, so a concurrent one can leave a key
-    # with both buckets taken; every such failure is validated below
+    # with both buckets taken (iceberg: its front and both backyard buckets);
+    # every such failure is validated below
     if scheme == "double" or load < 0.9:
         assert not full.any(), f"{full.sum()} inserts failed at load {load}"
     assert ((st == ost) | full).all()
@@ -165,7 +167,7 @@ def test_config2_small(ws, oracle_mod, scheme, meta, tile, load):
     if ufull.any():
         # the new keys take two-choice tables past 0.9 load: a key whose both
         # buckets are taken fails, and the layout must show both full
-        assert scheme == "p2" and load >= 0.9 and ufull.mean() < 0.02
+        assert scheme != "double" and load >= 0.9 and ufull.mean() < 0.02
         r, L = check_layout(oracle_mod, t)
         assert oracle_mod.candidates_full(L["slots"], L["tags"], L["nb"], L["B"], L["scheme"], L["pmax"],
                                           L["seed1"], L["seed2"], ukeys[ufull]).all()
@@ -287,15 +289,18 @@ def test_same_key_stress(ws, oracle_mod, scheme, meta, layout):
 @pytest.mark.parametrize("scheme,meta", DESIGNS, ids=DESIGN_IDS)
 def test_adversarial_every_bucket(ws, oracle_mod, scheme, meta):
     t = ws.Table(1 << 13, scheme, meta)
+    inf = t.info()
     nb = t.num_buckets()
+    npb = inf["front_buckets"]  # buckets that are some key's primary bucket
     cand = W.distinct_keys(31337, 64 * nb)
     pb = host(t.primary_bucket(dev(cand)))
-    assert (pb == oracle_mod.primary_bucket(cand, nb, t.info()["seed1"])).all()
+    assert (pb == oracle_mod.primary_bucket_of(inf["scheme"], cand, nb, inf["seed1"], inf["seed2"])).all()
     order = np.argsort(pb, kind="stable")
     spb, sk = pb[order], cand[order]
-    first = np.searchsorted(spb, np.arange(nb))
-    cnt = np.bincount(pb.astype(np.int64), minlength=nb)
-    assert (cnt >= 2).all()
+    first = np.searchsorted(spb, np.arange(npb))
+    cnt = np.bincount(pb.astype(np.int64), minlength=npb)
+    assert cnt.size == npb and (cnt >= 2).all()
+    nb = npb
     X, Y = sk[first], sk[first + 1]
     for rnd in range(10):
         t.clear()
@@ -361,12 +366,12 @@ def test_lock_timeout_is_bounded(ws, oracle_mod, scheme, meta):
     assert (host(v)[:500] == keys[:500] + np.uint64(1)).all()
     # plain inserts: two-choice placement needs the lock, double hashing does not
     st = host(t.insert(dev(keys[1000:]), dev(keys[1000:]), return_status=True))
-    want = ws.INSERTED if scheme == "double" else ws.FAIL_TIMEOUT
+    want = ws.INSERTED if scheme == "double" else ws.FAIL_TIMEOUT  # two-choice and iceberg lock
     assert (st == want).all()
     e = t.last_error()
     assert e["status"] == 5 and e["timeout"] == 500 + (0 if scheme == "double" else 500)
     t.debug_fill_locks(False)
-    rest = keys[500:] if scheme == "p2" else keys[500:1000]
+    rest = keys[500:] if scheme != "double" else keys[500:1000]
     assert (host(t.insert(dev(rest), dev(rest), return_status=True)) == ws.INSERTED).all()
     assert t.count() == 1500
     check_layout(oracle_mod, t, 1500)

@@ -367,6 +367,80 @@ def test_candidates_full_planted(oracle_mod):
     assert oracle_mod.candidates_full(s, None, nb, B, 1, 80, S1, S2, [k]).tolist() == [False]
 
 
+# --------------------------------------------------------------------------
+# iceberg geometry (front yard / backyard): invariants and planted layouts
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("nb", [4, 8, 64, 1024, 1 << 16])
+def test_iceberg_geometry_invariants(oracle_mod, nb):
+    keys = W.distinct_keys(11 + nb, 40 * nb if nb <= 1024 else 1 << 20)
+    g = oracle_mod.iceberg_buckets(keys, nb, S1, S2).astype(np.int64)
+    front, b1, b2 = g[:, 0], g[:, 1], g[:, 2]
+    n_front = int(b1.min())
+    # the front yard is a prefix, the backyard the rest; every bucket is used
+    assert front.max() < n_front <= min(b1.min(), b2.min()) and max(b1.max(), b2.max()) == nb - 1
+    assert np.unique(front).size == n_front and np.unique(np.concatenate([b1, b2])).size == nb - n_front
+    # a backyard of about 17% of the buckets, at least two
+    n_back = nb - n_front
+    assert n_back >= 2 and (nb < 64 or 0.16 <= n_back / nb <= 0.18)
+    assert (b1 != b2).all()
+    if nb >= 64:  # uniform front and backyard choices (chi-square, generous bound)
+        from scipy.stats import chisquare
+        assert chisquare(np.bincount(front, minlength=n_front)).pvalue > 1e-6
+        assert chisquare(np.bincount(b1 - n_front, minlength=n_back)).pvalue > 1e-6
+        assert chisquare(np.bincount(b2 - n_front, minlength=n_back)).pvalue > 1e-6
+
+
+def test_layout_checker_iceberg_planted(oracle_mod):
+    nb, B = 16, 32
+    S = nb * B
+    geo = lambda ks: oracle_mod.iceberg_buckets(np.asarray(ks, np.uint64), nb, S1, S2).astype(np.int64)
+
+    def fresh():
+        return np.zeros(2 * S, np.uint64), np.zeros(S, np.uint16)
+
+    def put(slots, tags, b, j, k, v=1):
+        slots[2 * (b * B + j)] = k
+        slots[2 * (b * B + j) + 1] = v
+        tags[b * B + j] = _tag(k)
+
+    chk = lambda s, t: oracle_mod.layout_check(s, t, nb, B, 2, 3, S1, S2)
+    k = 0x0123_4567_89AB_CDEF
+    f, c1, c2 = geo([k])[0]
+    s, t = fresh(); put(s, t, f, 0, k)
+    r = chk(s, t)
+    assert r["live"] == 1 and r["bad_bucket"] == 0 and r["early_exit"] == 0
+    other = next(b for b in range(nb) if b not in (f, c1, c2))
+    s, t = fresh(); put(s, t, other, 0, k)
+    assert chk(s, t)["bad_bucket"] == 1
+    # backyard copy while the front bucket still has an EMPTY slot
+    for c in (c1, c2):
+        s, t = fresh(); put(s, t, c, 0, k)
+        assert chk(s, t)["early_exit"] == 1 and chk(s, t)["bad_bucket"] == 0
+    # legal once the front bucket is full (fillers whose own front is f)
+    rng = random.Random(9)
+    fillers = []
+    while len(fillers) < B:
+        x = rng.getrandbits(64)
+        if x not in SENT and x != k and geo([x])[0][0] == f:
+            fillers.append(x)
+    for j, x in enumerate(fillers):
+        put(s, t, f, j, x)
+    r = chk(s, t)
+    assert r["early_exit"] == 0 and r["live"] == B + 1 and r["bad_bucket"] == 0
+    # a tombstone in the front does not make a backyard key illegal
+    t[f * B + 7], s[2 * (f * B + 7)] = 1, MASK
+    assert chk(s, t)["early_exit"] == 0
+    # candidate set full only when all three buckets are
+    s, t = fresh()
+    for b in (f, c1, c2):
+        for j in range(B):
+            put(s, t, b, j, 7000 + b * B + j)
+    full = lambda: oracle_mod.candidates_full(s, t, nb, B, 2, 3, S1, S2, [k]).tolist()
+    assert full() == [True]
+    t[c2 * B + 31] = 1  # a tombstone frees a slot of the second backyard bucket
+    assert full() == [False]
+
+
 def test_primary_bucket_is_h1(oracle_mod):
     keys = W.distinct_keys(3, 64)
     pb = oracle_mod.primary_bucket(keys, 1 << 10, S1)
