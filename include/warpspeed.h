@@ -160,7 +160,8 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  sequence one bucket per wave and takes the next op as soon as its op
  *  settles; ops the lanes cannot settle go to the tiles.  0 serves 32-op
  *  chunks (lane waves, then tiles for what is left), as batched and serving
- *  launches always do.
+ *  launches always do, and as insert-if-unique calls on two-choice and
+ *  iceberg tables do (their inserts lock: once per chunk beats once per wave).
  *  WS_OPT_LANE_WAVES (double hashing only; 0..255, 0 = default): buckets of a
  *  probe sequence the lane path follows, one per wave, before an op still
  *  open goes to the tiles.  Default: the whole sequence when streaming, 4 in

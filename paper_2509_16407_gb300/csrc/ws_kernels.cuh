@@ -940,7 +940,9 @@ struct TileOps {
   // snapshots of the probe sequence (wave w holds bucket w of every op still
   // open), the same rules as the tile probe.  lane_wave returns 1 when the op
   // is settled, 0 to go on to the next wave, -1 to hand it to the tile path
-  // (more than the snapshot can tell, a lost CAS, or a locked insert).
+  // (more than the snapshot can tell, or a lost CAS), and -2 when an upsert
+  // probed without the lock has proven its key absent: it must now take b_0's
+  // lock and read again before it may insert.
   // ----------------------------------------------------------------------
   // LW_INSERT_FREE: lock-free first-free insert (double hashing, no erase
   // in the launch).  LW_INSERT_LOCKED: the lane holds b_0's lock (or the
@@ -1022,7 +1024,7 @@ struct TileOps {
       st = ST_MISS;
       return 1;
     }
-    if (!ins) return -1;
+    if (!ins) return -2;  // absent, and this op holds no lock
     u64 fidx = ls.ff_idx, fk = ls.ff_k, fv = ls.ff_v;
     if (SCHEME == SCHEME_DOUBLE) {
       if (!sn.empty || !ls.ff_set) return -1;
@@ -1177,14 +1179,17 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
   // two-choice tables with plain 32-slot buckets read whole buckets instead
   // of first-line snapshots (below)
   constexpr bool kRounds = (SCHEME == SCHEME_P2) && !META && B == 32;
-  // An op that may insert an absent key under the lock takes b_0's lock
-  // from its own lane, one attempt; the lane's reads after it are then
-  // authoritative for K (only holders of b_0's lock insert K).  A lane that
-  // misses the lock leaves absent keys to the tiles, which wait for it.
+  // An insert-if-unique op that may insert under the lock (its key is most
+  // likely new) takes b_0's lock from its own lane, one attempt, before its
+  // first copy; the lane's reads after it are then authoritative for K (only
+  // holders of b_0's lock insert K).  Add / max / replace probe lock-free
+  // first: a present key -- a hot Zipf key above all -- needs no lock, and an
+  // absent one goes to the tiles, which lock and rescan.  A lane that misses
+  // the lock also leaves absent keys to the tiles, which wait for it.
   constexpr bool kLaneLock = (SCHEME == SCHEME_DOUBLE) || META || Ops::PRE_SLOTS == B || kRounds;
   const u64 b0 = Ops::bucket(tv, h1, h2, 0);
   bool locked = false;
-  if (kLaneLock && lane_ok && !done && opk == Ops::LW_UPDATE_ONLY) {
+  if (kLaneLock && lane_ok && !done && opk == Ops::LW_UPDATE_ONLY && (op == OP_INSERT || tv.phased)) {
     locked = tv.phased || Ops::lane_lock(tv, b0);  // bulk-synchronous: no locks
     if (locked) opk = Ops::LW_INSERT_LOCKED;
   }
@@ -1495,7 +1500,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           if (!lane_path) {
             state = L_PARKED;
           } else {
-            if (kLaneLock && opk == Ops::LW_UPDATE_ONLY) {
+            if (kLaneLock && opk == Ops::LW_UPDATE_ONLY && (op == OP_INSERT || tv.phased)) {
               locked = tv.phased || Ops::lane_lock(tv, Ops::bucket(tv, h1, h2, 0));
               if (locked) opk = Ops::LW_INSERT_LOCKED;
             }
@@ -1544,6 +1549,18 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           if (a.status_out) a.status_out[gi] = st;
           if (st >= ST_FULL) count_failure(tv, st);
           state = L_EMPTY;
+        } else if (r == -2 && kLaneLock && !locked &&
+                   Ops::lane_lock(tv, Ops::bucket(tv, sm.h1[lane], sm.h2[lane], 0))) {
+          // absent without the lock: now holding b_0's lock, follow the
+          // sequence again from b_0 and insert from what it reads
+          locked = true;
+          opk = Ops::LW_INSERT_LOCKED;
+          w = 0;
+          ls.ff_set = false;
+          ls.ff_idx = ls.ff_k = ls.ff_v = 0;
+          ls.occ0 = ls.occ1 = 0;
+          ls.f1_set = false;
+          ls.f1_idx = ls.f1_k = 0;
         } else if (r < 0 || w + 1 >= cap) {
           state = L_PARKED;
         } else {
@@ -1609,7 +1626,11 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
   const bool lockfree = (KIND == KIND_UPSERT);  // one call is one phase: no erase runs with it
   int dcount = 0;
   constexpr bool kRounds = (SCHEME == SCHEME_P2) && !META && B == 32;
-  if (kRounds || !tv.stream) {
+  // Insert-if-unique calls on tables whose inserts lock (two-choice,
+  // iceberg) take a lock for almost every op; streaming would pay that
+  // acquire once per wave instead of once per 32-op chunk.
+  const bool lock_bound = (KIND == KIND_UPSERT) && SCHEME != SCHEME_DOUBLE && a.op == OP_INSERT;
+  if (kRounds || !tv.stream || lock_bound) {
     // 32-op chunks, grid-stride
     const u64 nchunks = (a.n + 31) / 32;
     const u64 stride = (u64)gridDim.x * kWarps;
