@@ -493,9 +493,11 @@ def bench_e2e(args, tables, keys_slice, vals_slice, keys_pos, keys_neg, keys_up,
 # ---------------------------------------------------------------------------
 # the oracle on the host cores (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
-def oracle_step_sample(log2_slots=22, load=0.9, nq=1 << 18, seed=0xC0FFEE):
+def oracle_step_sample(log2_slots=22, load=0.9, nq=1 << 18, seed=0xC0FFEE, shard=0, n_shards=1):
     """One step of the same workload shape at 2^log2_slots slots, on the oracle.
-    Returns (ops, seconds) for one step (prefill untimed), plus a runner."""
+    Returns (ops, runner, description); the runner times one step (prefill
+    untimed).  With n_shards > 1 only the keys whose splitmix64 finaliser is
+    shard mod n_shards take part (one map per shard)."""
     import oracle
     S = 1 << log2_slots
     base_n = int(0.85 * S)
@@ -508,6 +510,11 @@ def oracle_step_sample(log2_slots=22, load=0.9, nq=1 << 18, seed=0xC0FFEE):
     pos = ks[:top_n][W.splitmix64(seed + 1, nq) % np.uint64(top_n)]
     up = base[W.splitmix64(seed + 2, nq) % np.uint64(base_n)]
     vu = W.uniform_int(seed + 3, nq, 1, 1000)
+    if n_shards > 1:
+        mine = lambda k: (W.mix13(k) % np.uint64(n_shards)) == np.uint64(shard)
+        mb, ms_, mp, mn, mu = mine(base), mine(slc), mine(pos), mine(neg), mine(up)
+        base, vb, slc, vs, pos, neg, up, vu = base[mb], vb[mb], slc[ms_], vs[ms_], pos[mp], neg[mn], up[mu], vu[mu]
+        base_n = base.size
     om = oracle.OracleMap()
     om.insert(base, vb)
 
@@ -522,7 +529,8 @@ def oracle_step_sample(log2_slots=22, load=0.9, nq=1 << 18, seed=0xC0FFEE):
         assert om.count() == base_n
         return dt
 
-    return 2 * slice_n + 3 * nq, run, f"2^{log2_slots}-slot-equivalent map at 0.85->{load} load, {2 * slice_n + 3 * nq} ops/step"
+    n_ops = 2 * slc.size + pos.size + neg.size + up.size
+    return n_ops, run, f"2^{log2_slots}-slot-equivalent map at 0.85->{load} load, {n_ops} ops/step"
 
 
 def cpu_baseline(seconds=10.0):
@@ -533,6 +541,30 @@ def cpu_baseline(seconds=10.0):
         done += ops
     return {"value": round(done / spent / 1e9, 6), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{desc}; {done} ops in {spent:.1f} s (single-threaded std::unordered_map)"}
+
+
+def _sharded_worker(args):
+    shard, n_shards, seconds = args
+    ops, run, _ = oracle_step_sample(shard=shard, n_shards=n_shards)
+    done, spent = 0, 0.0
+    while spent < seconds:
+        spent += run()
+        done += ops
+    return done, spent
+
+
+def cpu_baseline_sharded(seconds=10.0):
+    """The oracle on every host core: keys sharded by hash, one map per
+    process (spawn-started pool), throughput = all ops / the slowest shard."""
+    import multiprocessing as mp
+    n = max(1, os.cpu_count() or 1)
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_sharded_worker, [(r, n, seconds) for r in range(n)])
+    # each shard ran for `seconds`; scale every shard's rate to a common span
+    rate = sum(d / t for d, t in res)
+    return {"value": round(rate / 1e9, 6), "unit": UNIT, "cores": n, "kind": "oracle, sharded by key hash",
+            "sample": f"2^22-slot-equivalent workload split over {n} processes by splitmix64 finaliser of the key "
+                      f"mod {n}; each shard ran about {seconds:.0f} s; sum of the shards' rates"}
 
 
 def bench_reference(args, rank, world):
@@ -1039,6 +1071,7 @@ def main():
     if rank == 0:
         if not args.no_cpu:
             res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+            res["cpu_baseline_sharded"] = cpu_baseline_sharded(args.cpu_seconds)
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -186,6 +186,11 @@ __device__ __forceinline__ u32 atom_or_acquire(u32* p, u32 m) {
 __device__ __forceinline__ void red_and_release(u32* p, u32 m) {
   asm volatile("red.release.gpu.global.and.b32 [%0], %1;" ::"l"(p), "r"(m) : "memory");
 }
+// Unlock by a holder that wrote nothing under the lock (its key was present,
+// or its claim lost): there is nothing to publish, so no release.
+__device__ __forceinline__ void red_and_relaxed(u32* p, u32 m) {
+  asm volatile("red.relaxed.gpu.global.and.b32 [%0], %1;" ::"l"(p), "r"(m) : "memory");
+}
 
 __device__ __forceinline__ void red_add_u64(u64* p, u64 v) {
   asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");

@@ -79,14 +79,21 @@ __device__ __forceinline__ TileCtx<T> make_tile(int lane) {
   return c;
 }
 
-// First-probe snapshots of a warp's 32 ops, in shared memory, stored
-// slot-major with one spare column: a lane reading its own op's slots and a
-// tile reading one op's slots both hit distinct banks.  Plain tables: row s =
-// slot s of b_0 (s < 8).  Metadata tables: rows 0..3 = the 32 tags of b_0
-// (eight per row), row 4 = the first tag-matching slot's pair, row 5 .key =
-// that slot's index (~0 when no tag matched).
+// Bucket snapshots of a warp's 32 ops, in shared memory, op-major with one
+// spare slot per op (9 slots = 144 bytes): an asynchronous copy of an op's
+// 128-byte line lands in contiguous shared memory (one wavefront per line),
+// and 8 lanes reading slot s of their own ops hit distinct banks.  Plain
+// tables: slots 0..7 of op j = the first line of its bucket.  Metadata
+// tables: slots 0..3 = the bucket's 32 tags (eight per slot), slot 4 = the
+// first tag-matching slot's pair, slot 5 .key = that slot's index (~0 when no
+// tag matched).  The whole-bucket rounds view the same array flat: bucket q
+// of a round at [32 q, 32 q + 32).
+constexpr int kPreStride = 9;
 struct __align__(16) PreWarp {
-  Slot line[8][33];
+  Slot s[32 * kPreStride];
+  __device__ __forceinline__ Slot& at(int j, int k) { return s[j * kPreStride + k]; }
+  __device__ __forceinline__ const Slot& at(int j, int k) const { return s[j * kPreStride + k]; }
+  __device__ __forceinline__ Slot& flat(int q, int lane) { return s[q * 32 + lane]; }
 };
 constexpr u64 kNoCand = ~0ull;
 
@@ -95,10 +102,10 @@ struct PreRef {
   const PreWarp* w;
   int j;
   __device__ __forceinline__ bool ok() const { return w != nullptr; }
-  __device__ __forceinline__ Slot slot(int s) const { return w->line[s][j]; }
-  __device__ __forceinline__ const u16* tagrow(int r) const { return reinterpret_cast<const u16*>(&w->line[r][j]); }
-  __device__ __forceinline__ Slot cand() const { return w->line[4][j]; }
-  __device__ __forceinline__ u64 cand_idx() const { return w->line[5][j].key; }
+  __device__ __forceinline__ Slot slot(int k) const { return w->at(j, k); }
+  __device__ __forceinline__ const u16* tagrow(int r) const { return reinterpret_cast<const u16*>(&w->at(j, r)); }
+  __device__ __forceinline__ Slot cand() const { return w->at(j, 4); }
+  __device__ __forceinline__ u64 cand_idx() const { return w->at(j, 5).key; }
 };
 __device__ __forceinline__ PreRef no_pre() { return PreRef{nullptr, 0}; }
 
@@ -164,16 +171,16 @@ struct TileOps {
     int q = -1;
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
-      const u16* t = reinterpret_cast<const u16*>(&pw->line[r][j]);
+      const u16* t = reinterpret_cast<const u16*>(&pw->at(j, r));
 #pragma unroll
       for (int h = 0; h < 8; ++h)
         if (q < 0 && t[h] == kt) q = 8 * r + h;
     }
     if (q >= 0) {
-      ptx::cp_async16(&pw->line[4][j], tv.slots + b0 * 32 + (u64)q);
-      pw->line[5][j].key = b0 * 32 + (u64)q;
+      ptx::cp_async16(&pw->at(j, 4), tv.slots + b0 * 32 + (u64)q);
+      pw->at(j, 5).key = b0 * 32 + (u64)q;
     } else {
-      pw->line[5][j].key = kNoCand;
+      pw->at(j, 5).key = kNoCand;
     }
   }
 
@@ -686,9 +693,16 @@ struct TileOps {
     __syncwarp(c.mask);
   }
 
-  __device__ static __forceinline__ void unlock(const TableView& tv, const TileCtx<T>& c, u64 b) {
+  // Unlock; with release semantics only when the holder claimed a slot (the
+  // next holder must see it), relaxed when it wrote nothing under the lock.
+  __device__ static __forceinline__ void unlock(const TableView& tv, const TileCtx<T>& c, u64 b, bool wrote = true) {
     __syncwarp(c.mask);
-    if (c.tl == 0) ptx::red_and_release(tv.locks + (b >> 5), ~(1u << (b & 31)));
+    if (c.tl == 0) {
+      if (wrote)
+        ptx::red_and_release(tv.locks + (b >> 5), ~(1u << (b & 31)));
+      else
+        ptx::red_and_relaxed(tv.locks + (b >> 5), ~(1u << (b & 31)));
+    }
   }
 
   // One lock attempt by a single lane (no test first: one round trip).  A
@@ -697,8 +711,11 @@ struct TileOps {
     const u32 bit = 1u << (b & 31);
     return !(ptx::atom_or_acquire(tv.locks + (b >> 5), bit) & bit);
   }
-  __device__ static __forceinline__ void lane_unlock(const TableView& tv, u64 b) {
-    ptx::red_and_release(tv.locks + (b >> 5), ~(1u << (b & 31)));
+  __device__ static __forceinline__ void lane_unlock(const TableView& tv, u64 b, bool wrote) {
+    if (wrote)
+      ptx::red_and_release(tv.locks + (b >> 5), ~(1u << (b & 31)));
+    else
+      ptx::red_and_relaxed(tv.locks + (b >> 5), ~(1u << (b & 31)));
   }
 
   // Two-choice placement (§4.2) from both buckets' loads and first free
@@ -817,7 +834,7 @@ struct TileOps {
         break;
       }
     }
-    if (!tv.phased) unlock(tv, c, b0);
+    if (!tv.phased) unlock(tv, c, b0, st == ST_INSERTED);
     return st;
   }
 
@@ -1221,25 +1238,25 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
         const int nr = (n - r0) < 8 ? (n - r0) : 8;
 #pragma unroll
         for (int q = 0; q < 8; ++q)
-          if (q < nr) ptx::cp_async16(&sm.pre.line[q][lane], tv.slots + sm.bw[sm.list[r0 + q]] * 32 + (u64)lane);
+          if (q < nr) ptx::cp_async16(&sm.pre.flat(q, lane), tv.slots + sm.bw[sm.list[r0 + q]] * 32 + (u64)lane);
         ptx::cp_async_wait_all();
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           if (q >= nr) break;  // warp-uniform
           const int j = sm.list[r0 + q];
-          const u64 k = sm.pre.line[q][lane].key;
+          const u64 k = sm.pre.flat(q, lane).key;
           const unsigned mk = __ballot_sync(0xffffffffu, k == sm.key[j]);
           const unsigned mf = __ballot_sync(0xffffffffu, k == KEY_EMPTY || k == KEY_TOMB);
           if (lane == j) {
             occ = 32u - (u32)__popc(mf);
             if (mk) {
               hs = __ffs(mk) - 1;
-              hv = sm.pre.line[q][hs].val;
+              hv = sm.pre.flat(q, hs).val;
             }
             if (mf) {
               fs = __ffs(mf) - 1;
-              const Slot f = sm.pre.line[q][fs];
+              const Slot f = sm.pre.flat(q, fs);
               fk = f.key;
               fv = f.val;
             }
@@ -1327,14 +1344,14 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int j = i * 8 + (lane >> 2), part = lane & 3;
-        if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.line[part][j], tv.tags + sm.bw[j] * 32 + 8 * part);
+        if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.tags + sm.bw[j] * 32 + 8 * part);
       }
     } else {
       constexpr int PS = Ops::PRE_SLOTS;  // 8 slots = 128 B per op
 #pragma unroll
       for (int i = 0; i < PS; ++i) {
         const int j = i * (32 / PS) + lane / PS, part = lane % PS;
-        if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.line[part][j], tv.slots + sm.bw[j] * B + (u64)part);
+        if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.slots + sm.bw[j] * B + (u64)part);
       }
     }
     ptx::cp_async_wait_all();
@@ -1355,7 +1372,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     }
     __syncwarp();  // the next wave overwrites the snapshots
   }
-  if (locked && !tv.phased) Ops::lane_unlock(tv, b0);  // after the claim (release)
+  if (locked && !tv.phased) Ops::lane_unlock(tv, b0, done && st == ST_INSERTED);  // after the claim
   // the tile path may reuse a snapshot only if it is still of b_0 and fresh
   const unsigned pre_mask = __ballot_sync(0xffffffffu, snap_wave == 0 && fresh);
   sm.out[lane] = out;
@@ -1520,14 +1537,14 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int j = i * 8 + (lane >> 2), part = lane & 3;
-          if ((act >> j) & 1u) ptx::cp_async16(&sm.pre.line[part][j], tv.tags + sm.bw[j] * 32 + 8 * part);
+          if ((act >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.tags + sm.bw[j] * 32 + 8 * part);
         }
       } else {
         constexpr int PS = Ops::PRE_SLOTS;
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
           const int j = i * (32 / PS) + lane / PS, part = lane % PS;
-          if ((act >> j) & 1u) ptx::cp_async16(&sm.pre.line[part][j], tv.slots + sm.bw[j] * B + (u64)part);
+          if ((act >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.slots + sm.bw[j] * B + (u64)part);
         }
       }
       ptx::cp_async_wait_all();
@@ -1543,6 +1560,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
         u8 st = ST_MISS;
         const int r =
             Ops::lane_wave(tv, p, sm.key[lane], sm.val[lane], op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh);
+        const bool wrote = r > 0 && st == ST_INSERTED;
         if (r > 0) {
           const u64 gi = sm.out[lane];
           if (a.vals_out) a.vals_out[gi] = out;
@@ -1567,7 +1585,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           ++w;
         }
         if (state != L_ACTIVE && locked) {
-          if (!tv.phased) Ops::lane_unlock(tv, Ops::bucket(tv, sm.h1[lane], sm.h2[lane], 0));  // after the claim
+          if (!tv.phased) Ops::lane_unlock(tv, Ops::bucket(tv, sm.h1[lane], sm.h2[lane], 0), wrote);  // after the claim
           locked = false;
         }
       }
