@@ -226,6 +226,13 @@ def recorded_traffic():
 # ---------------------------------------------------------------------------
 # our implementation
 # ---------------------------------------------------------------------------
+def config2_workload(args, names):
+    """The default line's workload, as both arms name it."""
+    lq = int(np.log2(args.nq))
+    return (f"2^{args.log2_slots}-slot tables at {args.load} load (0.85 -> {args.load} slice insert,"
+            f" 2^{lq} positive + negative queries, 2^{lq} upsert-add, slice erase, count), designs {names}")
+
+
 def bench_ours(args, rank, world):
     import torch
     import paper_2509_16407_gb300 as ws
@@ -434,9 +441,7 @@ def bench_ours(args, rank, world):
         "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {
-            "workload": f"2^{args.log2_slots}-slot tables at {args.load} load (0.85 -> {args.load} slice insert,"
-                        f" 2^{int(np.log2(nq))} positive + negative queries, 2^{int(np.log2(nq))} upsert-add,"
-                        f" slice erase, count), designs {[d[2] for d in designs]}",
+            "workload": config2_workload(args, [d[2] for d in designs]),
             "slots": S, "load": args.load, "base_keys": base_n, "slice_keys": slice_n, "queries": nq,
             "ops_per_step": ops_per_step * world, "ops_per_step_per_gpu": ops_per_step,
             "tiles": {d[2]: t.info()["tile"] for d, (_, t) in zip(designs, tables)},
@@ -580,7 +585,9 @@ def bench_reference(args, rank, world):
     return {"metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(spent / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": desc, "parallelism": "1 host thread"},
+            "config": {"workload": config2_workload(args, [d[2] for d in DESIGNS]), "parallelism": "1 host thread",
+                       "sample": "each step runs the same phases on one map of the oracle at 2^22 slots "
+                                 f"(the workload's shape, scaled so the run ends in minutes): {desc}"},
             "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 

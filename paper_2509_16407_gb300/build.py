@@ -51,6 +51,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if force or _stale(o, [s] + hdrs):
             jobs.append((s, o))
     exe = nvcc()
+    # the multi-table kernels take longest: start them first
+    heavy = ("ws_batch.cu", "ws_noalloc.cu")
+    jobs.sort(key=lambda j: (os.path.basename(j[0]) not in heavy, j[0]))
 
     def compile_one(job):
         s, o = job

@@ -1,25 +1,20 @@
-// ws_inst_p2_plain.cu -- kernel instantiations: scheme SCHEME_P2, metadata false.
-// (Split across translation units so the build compiles them in parallel.)
+// ws_inst_p2_plain.cu -- dispatcher of the SCHEME_P2 plain instantiations, which
+// live in ws_inst_p2_plain_*.cu by bucket size (compiled in parallel).
 #include "ws_kernels.cuh"
 
 namespace ws {
 
-cudaError_t launch_p2_plain(int B, int T, const TableView& tv, const BatchArgs& a, int kind,
-                           cudaStream_t s, int sms) {
-  switch (B * 100 + T) {
-    case 804: return launch_cfg<SCHEME_P2, false, 8, 4>(tv, a, kind, s, sms);
-    case 808: return launch_cfg<SCHEME_P2, false, 8, 8>(tv, a, kind, s, sms);
-    case 816: return launch_cfg<SCHEME_P2, false, 8, 16>(tv, a, kind, s, sms);
-    case 832: return launch_cfg<SCHEME_P2, false, 8, 32>(tv, a, kind, s, sms);
-    case 1604: return launch_cfg<SCHEME_P2, false, 16, 4>(tv, a, kind, s, sms);
-    case 1608: return launch_cfg<SCHEME_P2, false, 16, 8>(tv, a, kind, s, sms);
-    case 1616: return launch_cfg<SCHEME_P2, false, 16, 16>(tv, a, kind, s, sms);
-    case 1632: return launch_cfg<SCHEME_P2, false, 16, 32>(tv, a, kind, s, sms);
-    case 3204: return launch_cfg<SCHEME_P2, false, 32, 4>(tv, a, kind, s, sms);
-    case 3208: return launch_cfg<SCHEME_P2, false, 32, 8>(tv, a, kind, s, sms);
-    case 3216: return launch_cfg<SCHEME_P2, false, 32, 16>(tv, a, kind, s, sms);
-    case 3232: return launch_cfg<SCHEME_P2, false, 32, 32>(tv, a, kind, s, sms);
-  }
+cudaError_t launch_p2_plain_b8(int B, int T, const TableView&, const BatchArgs&, int kind, cudaStream_t, int);
+cudaError_t launch_p2_plain_b16(int B, int T, const TableView&, const BatchArgs&, int kind, cudaStream_t, int);
+cudaError_t launch_p2_plain_b32n(int B, int T, const TableView&, const BatchArgs&, int kind, cudaStream_t, int);
+cudaError_t launch_p2_plain_b32w(int B, int T, const TableView&, const BatchArgs&, int kind, cudaStream_t, int);
+
+cudaError_t launch_p2_plain(int B, int T, const TableView& tv, const BatchArgs& a, int kind, cudaStream_t s,
+                              int sms) {
+  if (B == 8) return launch_p2_plain_b8(B, T, tv, a, kind, s, sms);
+  if (B == 16) return launch_p2_plain_b16(B, T, tv, a, kind, s, sms);
+  if (B == 32) return (T <= 8) ? launch_p2_plain_b32n(B, T, tv, a, kind, s, sms)
+                               : launch_p2_plain_b32w(B, T, tv, a, kind, s, sms);
   return cudaErrorInvalidValue;
 }
 

@@ -1,0 +1,15 @@
+// ws_inst_p2_plain_b32w.cu -- kernel instantiations: scheme SCHEME_P2, metadata false,
+// 32-slot buckets, tiles 16 and 32.  (Split across translation units so the build compiles them in parallel.)
+#include "ws_kernels.cuh"
+
+namespace ws {
+
+cudaError_t launch_p2_plain_b32w(int B, int T, const TableView& tv, const BatchArgs& a, int kind, cudaStream_t s, int sms) {
+  switch (B * 100 + T) {
+    case 3216: return launch_cfg<SCHEME_P2, false, 32, 16>(tv, a, kind, s, sms);
+    case 3232: return launch_cfg<SCHEME_P2, false, 32, 32>(tv, a, kind, s, sms);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ws

@@ -972,7 +972,98 @@ struct TileOps {
     u32 occ1;     // iceberg: load and first free tag of the first backyard bucket (wave 1)
     bool f1_set;
     u64 f1_idx, f1_k;
+    u64 f1_v;     // two-choice by lines: observed value of b_1's first free slot
+    u32 cur_occ;  // two-choice by lines: occupied slots of the current bucket so far
+    u32 next_w;   // two-choice by lines: the wave to run next
   };
+
+  // Two-choice tables whose buckets are wider than a snapshot line: wave w
+  // reads line w % L of candidate bucket w / L (L = B / 8 lines per bucket),
+  // so a lane stops at the key or at the first EMPTY slot instead of reading
+  // whole buckets.  Occupancy and first free slot accumulate per bucket for
+  // the placement rule.  Streaming lanes only (lanes sit at different waves).
+  static constexpr bool kLines = (SCHEME == SCHEME_P2) && !META && PRE_SLOTS < B;
+  static constexpr u32 kLinesPerBucket = (u32)(B / PRE_SLOTS);
+  __device__ static __forceinline__ u32 wave_bucket(u32 w) { return kLines ? w / kLinesPerBucket : w; }
+  __device__ static __forceinline__ u32 wave_line(u32 w) { return kLines ? w % kLinesPerBucket : 0u; }
+
+  __device__ static __forceinline__ int lane_wave_lines(const TableView& tv, PreRef p, u64 K, u64 V, int op, int opk,
+                                                        u32 w, u64 bw, LaneState& ls, u64& out, u8& st,
+                                                        int& dcount, bool& fresh) {
+    const u32 c = w / kLinesPerBucket, l = w % kLinesPerBucket;
+    const u64 line0 = bw * B + (u64)l * PRE_SLOTS;
+    const Snap sn = snap_of(p, K);
+    if (sn.hit >= 0) {
+      const u64 idx = line0 + (u64)sn.hit;
+      const u64 v = p.slot(sn.hit).val;
+      if (opk == LW_QUERY) {
+        out = v;
+        st = ST_FOUND;
+        return 1;
+      }
+      if (opk != LW_ERASE) {
+        apply(tv, idx, op, V);
+        st = ST_FOUND;
+        return 1;
+      }
+      if (!ptx::cas_slot(tv.slots + idx, K, v, KEY_TOMB, 0)) {
+        fresh = false;
+        return -1;
+      }
+      out = v;
+      --dcount;
+      st = ST_FOUND;
+      return 1;
+    }
+    if (l == 0) ls.cur_occ = 0;
+    ls.cur_occ += sn.occ;
+    if (sn.ffree >= 0) {
+      const Slot o = p.slot(sn.ffree);
+      if (c == 0 && !ls.ff_set) {
+        ls.ff_set = true;
+        ls.ff_idx = line0 + (u64)sn.ffree;
+        ls.ff_k = o.key;
+        ls.ff_v = o.val;
+      } else if (c == 1 && !ls.f1_set) {
+        ls.f1_set = true;
+        ls.f1_idx = line0 + (u64)sn.ffree;
+        ls.f1_k = o.key;
+        ls.f1_v = o.val;
+      }
+    }
+    if (!sn.empty && l + 1 < kLinesPerBucket) {  // the bucket goes on
+      ls.next_w = w + 1;
+      return 0;
+    }
+    if (c == 0) {  // b_0 done (an EMPTY slot ends a bucket: EMPTY slots are a suffix)
+      ls.occ0 = ls.cur_occ;
+      if (!(nprobe(tv) == 1 || (tv.shortcut && ls.occ0 < FILL_SHORTCUT))) {
+        ls.next_w = kLinesPerBucket;  // b_1, line 0
+        return 0;
+      }
+    }
+    // K is in neither bucket
+    if (opk == LW_QUERY || opk == LW_ERASE) {
+      out = 0;
+      st = ST_MISS;
+      return 1;
+    }
+    if (opk != LW_INSERT_LOCKED) return -2;  // absent, and this op holds no lock
+    const int ch = p2_choice(ls.occ0, ls.ff_set, ls.cur_occ, ls.f1_set, c == 1);
+    if (ch < 0) {
+      st = ST_FULL;
+      return 1;
+    }
+    const bool ok = ch == 0 ? ptx::cas_slot(tv.slots + ls.ff_idx, ls.ff_k, ls.ff_v, K, V)
+                            : ptx::cas_slot(tv.slots + ls.f1_idx, ls.f1_k, ls.f1_v, K, V);
+    if (!ok) {
+      fresh = false;
+      return -1;
+    }
+    ++dcount;
+    st = ST_INSERTED;
+    return 1;
+  }
 
   __device__ static __forceinline__ int lane_wave(const TableView& tv, PreRef p, u64 K, u64 V, int op, int opk,
                                                   u32 w, u64 bw, LaneState& ls, u64& out, u8& st, int& dcount,
@@ -1448,7 +1539,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
   enum { L_EMPTY = 0, L_ACTIVE = 1, L_PARKED = 2 };
   constexpr int NT = 32 / T;
   constexpr unsigned kAll = 0xffffffffu;
-  constexpr bool kLaneLock = (SCHEME == SCHEME_DOUBLE) || META || Ops::PRE_SLOTS == B;
+  constexpr bool kLaneLock = (SCHEME == SCHEME_DOUBLE) || META || Ops::PRE_SLOTS == B || Ops::kLines;
   const u64 ks = a.key_stride ? a.key_stride : 1;
   const bool lane_path = (KIND != KIND_PROBE) && tv.preload;
   // a cap on the waves of one op (WS_OPT_LANE_WAVES); by default the whole sequence
@@ -1510,9 +1601,9 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           fresh = true;
           ls.ff_set = false;
           ls.ff_idx = ls.ff_k = ls.ff_v = 0;
-          ls.occ0 = ls.occ1 = 0;
+          ls.occ0 = ls.occ1 = ls.cur_occ = ls.next_w = 0;
           ls.f1_set = false;
-          ls.f1_idx = ls.f1_k = 0;
+          ls.f1_idx = ls.f1_k = ls.f1_v = 0;
           locked = false;
           if (!lane_path) {
             state = L_PARKED;
@@ -1531,7 +1622,8 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
     // 2. one wave: copy each active lane's current bucket, then settle
     const unsigned act = __ballot_sync(kAll, state == L_ACTIVE);
     if (act) {
-      sm.bw[lane] = (state == L_ACTIVE) ? Ops::bucket(tv, sm.h1[lane], sm.h2[lane], w) : 0;
+      sm.bw[lane] = (state == L_ACTIVE) ? Ops::bucket(tv, sm.h1[lane], sm.h2[lane], Ops::wave_bucket(w)) : 0;
+      if (Ops::kLines) sm.fresh[lane] = (u8)Ops::wave_line(w);  // which line of the bucket
       __syncwarp();
       if (META) {
 #pragma unroll
@@ -1544,7 +1636,8 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
 #pragma unroll
         for (int i = 0; i < PS; ++i) {
           const int j = i * (32 / PS) + lane / PS, part = lane % PS;
-          if ((act >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.slots + sm.bw[j] * B + (u64)part);
+          const u64 line = Ops::kLines ? (u64)sm.fresh[j] * PS : 0;
+          if ((act >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.slots + sm.bw[j] * B + line + (u64)part);
         }
       }
       ptx::cp_async_wait_all();
@@ -1558,8 +1651,12 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
         const PreRef p{&sm.pre, lane};
         u64 out = 0;
         u8 st = ST_MISS;
-        const int r =
-            Ops::lane_wave(tv, p, sm.key[lane], sm.val[lane], op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh);
+        int r;
+        if constexpr (Ops::kLines)
+          r = Ops::lane_wave_lines(tv, p, sm.key[lane], sm.val[lane], op, opk, w, sm.bw[lane], ls, out, st, dcount,
+                                   fresh);
+        else
+          r = Ops::lane_wave(tv, p, sm.key[lane], sm.val[lane], op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh);
         const bool wrote = r > 0 && st == ST_INSERTED;
         if (r > 0) {
           const u64 gi = sm.out[lane];
@@ -1576,13 +1673,13 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           w = 0;
           ls.ff_set = false;
           ls.ff_idx = ls.ff_k = ls.ff_v = 0;
-          ls.occ0 = ls.occ1 = 0;
+          ls.occ0 = ls.occ1 = ls.cur_occ = ls.next_w = 0;
           ls.f1_set = false;
-          ls.f1_idx = ls.f1_k = 0;
+          ls.f1_idx = ls.f1_k = ls.f1_v = 0;
         } else if (r < 0 || w + 1 >= cap) {
           state = L_PARKED;
         } else {
-          ++w;
+          w = Ops::kLines ? ls.next_w : w + 1;
         }
         if (state != L_ACTIVE && locked) {
           if (!tv.phased) Ops::lane_unlock(tv, Ops::bucket(tv, sm.h1[lane], sm.h2[lane], 0), wrote);  // after the claim
@@ -1643,12 +1740,19 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
   __syncthreads();
   const bool lockfree = (KIND == KIND_UPSERT);  // one call is one phase: no erase runs with it
   int dcount = 0;
-  constexpr bool kRounds = (SCHEME == SCHEME_P2) && !META && B == 32;
   // Insert-if-unique calls on tables whose inserts lock (two-choice,
   // iceberg) take a lock for almost every op; streaming would pay that
-  // acquire once per wave instead of once per 32-op chunk.
+  // acquire once per wave instead of once per 32-op chunk.  Plain
+  // two-choice tables with 32-slot buckets read whole buckets in 32-op
+  // chunks (rounds) for queries and erases too: a negative query or an
+  // erase of a late key needs most of both buckets, which rounds fetch in
+  // fewer dependent steps than streaming lanes reading a line per wave
+  // (measured at 2^28 slots: negative queries 2.56 ms in rounds vs 3.54 by
+  // lines, positive queries 1.51 vs 1.31, upserts 1.87 vs 1.66).
+  constexpr bool kRounds = (SCHEME == SCHEME_P2) && !META && B == 32;
   const bool lock_bound = (KIND == KIND_UPSERT) && SCHEME != SCHEME_DOUBLE && a.op == OP_INSERT;
-  if (kRounds || !tv.stream || lock_bound) {
+  const bool rounds = kRounds && (KIND == KIND_QUERY || KIND == KIND_ERASE);
+  if (!tv.stream || lock_bound || rounds) {
     // 32-op chunks, grid-stride
     const u64 nchunks = (a.n + 31) / 32;
     const u64 stride = (u64)gridDim.x * kWarps;
