@@ -288,7 +288,7 @@ ws_status ws_batch_plan_destroy(ws_batch_plan* plan);
  * critical loops that cannot take cudaFree's device-wide synchronisation.
  * Same items and semantics as a one-phase-at-a-time ws_batch_plan, run directly
  * (no graph), with the plan's scratch (descriptors, chunk map, work tickets)
- * kept in one fixed device array inside the library (~170 KiB on every GPU
+ * kept in one fixed device array inside the library (~193 KiB on every GPU
  * that loads the library, held until exit) instead of allocated memory.
  * Limits: at most 1024 items and 16 distinct phases per call; larger calls
  * return WS_ERR_INVALID and ws_cuda_error_string() says why.  The first call
@@ -306,9 +306,11 @@ ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n_items, ws_
  * first, at most one request per table in flight) in one persistent
  * multi-table kernel.  Each result therefore equals that of replaying its
  * table's requests alone in arrival order.  Tables are admitted only while
- * free device memory stays above hbm_headroom of the total; a table about to
+ * free device memory (counting memory the device's default stream-ordered
+ * pool holds unused) stays above hbm_headroom of the total; a table about to
  * pass grow_at load is rehashed into one twice as large when memory admits
- * it.  plain = 1 serves one request per launch, one launch at a time (the
+ * it.  Creating a server sets the default pool's release threshold to keep
+ * freed memory (grown-out tables) pooled for later growth.  plain = 1 serves one request per launch, one launch at a time (the
  * per-request baseline). */
 typedef struct ws_server ws_server;
 typedef struct {

@@ -1,5 +1,6 @@
 // ws_batch.cu -- batched mode: many tables and their op batches in one
-// persistent kernel per phase, captured once into a CUDA graph.
+// persistent kernel per phase and (menu entry, op kind) group, captured once
+// into a CUDA graph.
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -11,10 +12,15 @@
 using namespace wsi;
 
 struct ws_batch_plan {
+  struct Group {  // chunks of one menu entry and op kind, one persistent launch
+    int cfg = 0, kind = 0;
+    size_t chunk_off = 0, n_chunks = 0;
+  };
   struct Phase {
     size_t item_off = 0, n_items = 0, chunk_off = 0, n_chunks = 0;
+    std::vector<Group> groups;
   };
-  int device = 0, num_sms = 0, grid = 0;
+  int device = 0, num_sms = 0;
   std::vector<ws_batch_item> src;     // the caller's items, sorted by phase then size
   std::vector<int> src_phase_rank;    // dense phase index of each item
   std::vector<ws::MultiItem> items;   // device descriptors, one per menu item
@@ -85,12 +91,23 @@ ws_status build(ws_batch_plan* p) {
     ws_batch_plan::Phase& P = p->phases[(size_t)ph];
     P.item_off = p->items.size();
     P.chunk_off = p->chunks.size();
+    // the phase's menu items grouped by (menu entry, kind), larger items first
+    // inside a group (the src order): one persistent launch per group
+    std::vector<size_t> sel;
     for (size_t i = 0; i < p->src.size(); ++i) {
-      if (p->src_phase_rank[i] != ph) continue;
+      if (p->src_phase_rank[i] != ph || p->src[i].n == 0) continue;
+      const ws_table* t = p->src[i].table;
+      if (ws::multi_menu_index(t->scheme, t->meta != 0, (int)t->B, t->T) >= 0) sel.push_back(i);
+    }
+    auto key_of = [&](size_t i) {
+      const ws_table* t = p->src[i].table;
+      return ws::multi_menu_index(t->scheme, t->meta != 0, (int)t->B, t->T) * 8 + kind_of(p->src[i].kind);
+    };
+    std::stable_sort(sel.begin(), sel.end(), [&](size_t x, size_t y) { return key_of(x) < key_of(y); });
+    for (size_t i : sel) {
       const ws_batch_item& s = p->src[i];
       const ws_table* t = s.table;
       const int cfg = ws::multi_menu_index(t->scheme, t->meta != 0, (int)t->B, t->T);
-      if (cfg < 0 || s.n == 0) continue;  // fallback launch (or nothing to do)
       ws::MultiItem m;
       std::memset(&m, 0, sizeof(m));
       m.tv = view_for(p, t);
@@ -109,12 +126,20 @@ ws_status build(ws_batch_plan* p) {
       const u32 idx = (u32)p->items.size();
       p->menu_item_of[i] = (int)idx;
       p->items.push_back(m);
+      if (P.groups.empty() || P.groups.back().cfg != cfg || P.groups.back().kind != m.kind) {
+        ws_batch_plan::Group G;
+        G.cfg = cfg;
+        G.kind = m.kind;
+        G.chunk_off = p->chunks.size();
+        P.groups.push_back(G);
+      }
       for (u64 st = 0; st < s.n; st += ws::kMultiChunk) {
         ws::MultiChunk c;
         c.item = idx;
         c.pad = 0;
         c.start = st;
         p->chunks.push_back(c);
+        ++P.groups.back().n_chunks;
       }
     }
     P.n_items = p->items.size() - P.item_off;
@@ -129,22 +154,22 @@ ws_status build(ws_batch_plan* p) {
     WS_CUDA(cudaMemcpy(p->d_chunks, p->chunks.data(), p->chunks.size() * sizeof(ws::MultiChunk),
                        cudaMemcpyHostToDevice));
   }
-  WS_CUDA(cudaMalloc(&p->d_tickets, (size_t)(nph > 0 ? nph : 1) * sizeof(u32)));
-  int occ = 0;
-  WS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ws::multi_kernel, ws::kThreads, 0));
-  p->grid = (occ > 0 ? occ : 1) * p->num_sms;
+  size_t n_groups = 0;
+  for (const ws_batch_plan::Phase& P : p->phases) n_groups += P.groups.size();
+  WS_CUDA(cudaMalloc(&p->d_tickets, (n_groups > 0 ? n_groups : 1) * sizeof(u32)));
 
   WS_CUDA(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
   cudaError_t err = cudaSuccess;
+  size_t gi = 0;
   for (int ph = 0; ph < nph && err == cudaSuccess; ++ph) {
     const ws_batch_plan::Phase& P = p->phases[(size_t)ph];
-    if (P.n_chunks) {
-      err = cudaMemsetAsync(p->d_tickets + ph, 0, sizeof(u32), p->cap);
+    for (const ws_batch_plan::Group& G : P.groups) {
+      if (err != cudaSuccess) break;
+      u32* ticket = p->d_tickets + gi++;
+      err = cudaMemsetAsync(ticket, 0, sizeof(u32), p->cap);
       if (err == cudaSuccess) {
-        const unsigned g = (unsigned)std::min<u64>((u64)p->grid, P.n_chunks);
-        ws::multi_kernel<<<g, ws::kThreads, 0, p->cap>>>(p->d_items, p->d_chunks + P.chunk_off, (u32)P.n_chunks,
-                                                          p->d_tickets + ph);
-        err = cudaGetLastError();
+        ws::MultiGroup g{p->d_items, p->d_chunks + G.chunk_off, nullptr, 0, 0, (u32)G.n_chunks, ticket};
+        err = ws::launch_multi(G.cfg, G.kind, g, p->cap, p->num_sms);
       }
     }
     for (size_t i = 0; i < p->src.size() && err == cudaSuccess; ++i) {

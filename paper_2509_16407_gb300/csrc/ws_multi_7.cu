@@ -1,0 +1,11 @@
+// ws_multi_7.cu -- persistent multi-table kernels of menu entry 7
+// (SCHEME_P2, metadata true, 32-slot buckets, tile 8), one per op kind.
+#include "ws_multi_kernel.cuh"
+
+namespace ws {
+
+cudaError_t launch_multi_7(int kind, const MultiGroup& g, cudaStream_t s, int num_sms) {
+  return launch_multi_cfg<SCHEME_P2, true, 32, 8>(kind, g, s, num_sms);
+}
+
+}  // namespace ws

@@ -10,7 +10,7 @@
 // scratch in one fixed, file-scope device array instead, so a call
 // allocates nothing.
 //
-// The array (kScratchBytes, about 170 KiB) exists on every GPU that loads
+// The array (kScratchBytes, about 193 KiB) exists on every GPU that loads
 // the library until the process exits.  Its device address is looked up once
 // per device, on the first call that uses that device (cudaGetSymbolAddress
 // with the device current); make that first call before any stream capture.
@@ -23,7 +23,6 @@
 #include <mutex>
 
 #include "ws_internal.h"
-#define WS_MULTI_NO_KERNEL
 #include "ws_multi.cuh"
 
 using namespace wsi;
@@ -36,9 +35,9 @@ constexpr int kMaxDevices = 64;
 
 // Layout of the scratch array.
 struct NoallocScratch {
-  u32 tickets[kMaxPhases];        // one work ticket per phase, zeroed by every call
-  u32 prefix[kMaxItems + 1];      // chunk prefix sums over the (phase-sorted) items
-  u32 pad[(256 - ((kMaxPhases + kMaxItems + 1) * 4) % 256) / 4];
+  u32 tickets[kMaxItems];         // one work ticket per launch group, zeroed by every call
+  u32 prefix[kMaxItems + 1];      // chunk prefix sums over the (phase, entry, kind)-sorted items
+  u32 pad[(256 - ((kMaxItems + kMaxItems + 1) * 4) % 256) / 4];
   ws::MultiItem items[kMaxItems];
 };
 constexpr size_t kScratchBytes = sizeof(NoallocScratch);
@@ -60,71 +59,6 @@ cudaError_t scratch_for(int dev, NoallocScratch** out) {
   }
   *out = g_scratch_of[dev];
   return cudaSuccess;
-}
-
-// The persistent multi-table kernel, reading its chunk map from the prefix
-// sums of the scratch array: chunk g belongs to the item i with
-// prefix[i] <= g < prefix[i + 1].  Items [i0, i1) form one phase.
-__global__ void __launch_bounds__(ws::kThreads, 2)
-    multi_kernel_prefix(const ws::MultiItem* __restrict__ items, const u32* __restrict__ prefix, u32 i0, u32 i1,
-                        u32* ticket) {
-  __shared__ ws::WarpSmem s_w[ws::kWarps];
-  __shared__ u32 s_item;
-  __shared__ u64 s_start;
-  __shared__ int s_stop;
-  __shared__ __align__(16) ws::MultiItem s_it;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const u32 first = prefix[i0], count = prefix[i1] - prefix[i0];
-  u32 cur_item = 0xffffffffu;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const u32 c = atomicAdd(ticket, 1u);
-      s_stop = c >= count;
-      if (!s_stop) {
-        const u32 g = first + c;
-        u32 lo = i0, hi = i1 - 1;  // largest i with prefix[i] <= g
-        while (lo < hi) {
-          const u32 mid = (lo + hi + 1) / 2;
-          if (prefix[mid] <= g)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
-        s_item = lo;
-        s_start = (u64)(g - prefix[lo]) * ws::kMultiChunk;
-      }
-    }
-    __syncthreads();
-    if (s_stop) break;
-    const u32 item = s_item;
-    const u64 start = s_start;
-    if (item != cur_item) {
-      const u64* src = reinterpret_cast<const u64*>(items + item);
-      u64* dst = reinterpret_cast<u64*>(&s_it);
-      for (int q = threadIdx.x; q < (int)(sizeof(ws::MultiItem) / 8); q += blockDim.x) dst[q] = src[q];
-      cur_item = item;
-    }
-    __syncthreads();
-    const ws::MultiItem& it = s_it;
-    const u64 base = start + (u64)w * 32;
-    int d = 0;
-    if (base < it.a.n) {
-      switch (it.cfg) {
-#define WS_NOALLOC_CASE(ID, SCH, MT, BB, TT)                   \
-  case ID:                                                     \
-    d = ws::multi_warp<ws::SCH, MT, BB, TT>(it, base, s_w[w], lane); \
-    break;
-        WS_MULTI_MENU(WS_NOALLOC_CASE)
-#undef WS_NOALLOC_CASE
-        default: break;
-      }
-    }
-    if (it.kind != ws::KIND_QUERY) {
-      d = __reduce_add_sync(0xffffffffu, d);
-      if (lane == 0 && d) atomicAdd((unsigned long long*)&it.tv.ctr->count, (unsigned long long)(long long)d);
-    }
-    __syncthreads();
-  }
 }
 
 int kind_of(int bk) {
@@ -180,10 +114,18 @@ extern "C" ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n
   WS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
 
   HostStage& hs = t_stage;
-  // stable order by phase (insertion sort: at most kMaxItems, no allocation)
+  // stable order by (phase, menu entry, kind) -- insertion sort: at most
+  // kMaxItems, no allocation; the items of one (entry, kind) run of a phase
+  // form one persistent launch
+  auto sort_key = [&](uint32_t i) {
+    const ws_table* t = items[i].table;
+    const int cfg = ws::multi_menu_index(t->scheme, t->meta != 0, (int)t->B, t->T);
+    return ((int64_t)items[i].phase * 16 + (cfg + 1)) * 8 + kind_of(items[i].kind);
+  };
   for (uint32_t i = 0; i < (uint32_t)n_items; ++i) {
     uint32_t k = i;
-    while (k > 0 && items[hs.order[k - 1]].phase > items[i].phase) {
+    const int64_t ki = sort_key(i);
+    while (k > 0 && sort_key(hs.order[k - 1]) > ki) {
       hs.order[k] = hs.order[k - 1];
       --k;
     }
@@ -243,16 +185,18 @@ extern "C" ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n
   WS_CUDA(cudaMemcpyAsync(scratch->prefix, hs.prefix, (n_items + 1) * sizeof(u32), cudaMemcpyHostToDevice, st));
   WS_CUDA(cudaMemcpyAsync(scratch->items, hs.items, n_items * sizeof(ws::MultiItem), cudaMemcpyHostToDevice, st));
   WS_CUDA(cudaMemsetAsync(scratch->tickets, 0, sizeof(scratch->tickets), st));
-  int occ = 0;
-  WS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, multi_kernel_prefix, ws::kThreads, 0));
-  const u64 grid_cap = (u64)(occ > 0 ? occ : 1) * (u64)num_sms;
+  uint32_t n_groups = 0;
   for (uint32_t p = 0; p < n_ph; ++p) {
     const uint32_t i0 = hs.phase_begin[p], i1 = hs.phase_begin[p + 1];
-    const u64 nch = hs.prefix[i1] - hs.prefix[i0];
-    if (nch) {
-      const unsigned g = (unsigned)(nch < grid_cap ? nch : grid_cap);
-      multi_kernel_prefix<<<g, ws::kThreads, 0, st>>>(scratch->items, scratch->prefix, i0, i1, scratch->tickets + p);
-      WS_CUDA(cudaGetLastError());
+    for (uint32_t g0 = i0; g0 < i1;) {  // runs of one (menu entry, kind)
+      uint32_t g1 = g0 + 1;
+      while (g1 < i1 && hs.items[g1].cfg == hs.items[g0].cfg && hs.items[g1].kind == hs.items[g0].kind) ++g1;
+      const u32 nch = hs.prefix[g1] - hs.prefix[g0];
+      if (hs.items[g0].cfg >= 0 && nch) {
+        ws::MultiGroup g{scratch->items, nullptr, scratch->prefix, g0, g1, nch, scratch->tickets + n_groups++};
+        WS_CUDA(ws::launch_multi(hs.items[g0].cfg, hs.items[g0].kind, g, st, num_sms));
+      }
+      g0 = g1;
     }
     for (uint32_t k = i0; k < i1; ++k) {  // configurations outside the menu
       const ws::MultiItem& m = hs.items[k];

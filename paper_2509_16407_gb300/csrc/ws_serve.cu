@@ -28,14 +28,7 @@
 #include <vector>
 
 #include "ws_internal.h"
-#define WS_MULTI_NO_KERNEL
 #include "ws_multi.cuh"
-
-namespace ws {
-// The persistent multi-table kernel (defined with the batch plans).
-__global__ void multi_kernel(const MultiItem* __restrict__ items, const MultiChunk* __restrict__ chunks, u32 n_chunks,
-                             u32* ticket);
-}  // namespace ws
 
 using namespace wsi;
 
@@ -70,7 +63,7 @@ struct Slot {
   u8* d_st = nullptr;
   ws::MultiItem* d_items = nullptr;
   ws::MultiChunk* d_chunks = nullptr;
-  u32* d_ticket = nullptr;
+  u32* d_ticket = nullptr;             // one work ticket per menu entry
   ws::MultiItem* h_items = nullptr;   // pinned
   ws::MultiChunk* h_chunks = nullptr; // pinned
   u64* h_counts = nullptr;            // pinned, one per request
@@ -84,7 +77,7 @@ struct Slot {
 
 struct ws_server {
   ws_server_config cfg;
-  int device = 0, num_sms = 0, occ = 1;
+  int device = 0, num_sms = 0;
   u64 max_chunks = 0;
   std::vector<STable> tables;
   std::vector<SReq> reqs;  // index = id
@@ -122,12 +115,29 @@ bool slot_alloc(Slot& sl, u64 cap, u64 max_items, u64 max_chunks) {
             cudaMalloc(&sl.d_st, cap) == cudaSuccess &&
             cudaMalloc(&sl.d_items, max_items * sizeof(ws::MultiItem)) == cudaSuccess &&
             cudaMalloc(&sl.d_chunks, max_chunks * sizeof(ws::MultiChunk)) == cudaSuccess &&
-            cudaMalloc(&sl.d_ticket, sizeof(u32)) == cudaSuccess &&
+            cudaMalloc(&sl.d_ticket, ws::kMultiMenu * sizeof(u32)) == cudaSuccess &&
             cudaMallocHost(&sl.h_items, max_items * sizeof(ws::MultiItem)) == cudaSuccess &&
             cudaMallocHost(&sl.h_chunks, max_chunks * sizeof(ws::MultiChunk)) == cudaSuccess &&
             cudaMallocHost(&sl.h_counts, max_items * sizeof(u64)) == cudaSuccess;
   if (!ok) cudaGetLastError();
   return ok;
+}
+
+// Device memory a new table may take: free memory plus what the default pool
+// holds but does not use (freed tables stay pooled, see ws_server_create).
+bool avail_bytes(int dev, size_t* avail, size_t* total) {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return false;
+  cudaMemPool_t pool;
+  uint64_t reserved = 0, used = 0;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess &&
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &reserved) == cudaSuccess &&
+      cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) == cudaSuccess && reserved > used)
+    fr += (size_t)(reserved - used);
+  cudaGetLastError();
+  *avail = fr;
+  *total = tot;
+  return true;
 }
 
 // Replace table `ti` by one `factor` times larger if memory admits it; the
@@ -138,7 +148,7 @@ bool try_grow(ws_server* sv, uint32_t ti, uint64_t need_live, Slot& sl) {
   while ((double)need_live > sv->cfg.grow_at * (double)cap) cap *= 2;
   if (cap == old->S) return false;
   size_t fr = 0, tot = 0;
-  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return false;
+  if (!avail_bytes(sv->device, &fr, &tot)) return false;
   const double bytes = (double)cap * (16.0 + (old->meta ? 2.0 : 0.0));
   if ((double)fr - bytes < sv->cfg.hbm_headroom * (double)tot) return false;  // not admitted
   ws_config c;
@@ -218,10 +228,17 @@ bool launch_slot(ws_server* sv, Slot& sl) {
     m.a = ws::BatchArgs{sl.d_keys + off, sl.d_vals + off, sl.d_ops + off, sl.d_out + off, sl.d_st + off, n, 0, 1, 0};
     m.kind = ws::KIND_MIXED;
     m.cfg = sv->cfg.plain ? -1 : ws::multi_menu_index(t->scheme, t->meta != 0, (int)t->B, t->T);
-    if (m.cfg < 0) {
-      fallback.push_back((int)i);
-    } else {
-      for (u64 st = 0; st < n; st += ws::kMultiChunk) {
+    if (m.cfg < 0) fallback.push_back((int)i);
+    off += n;
+  }
+  // chunks grouped by menu entry (every request is a mixed batch): one
+  // persistent launch per entry present
+  u64 group_off[ws::kMultiMenu + 1] = {0};
+  for (int cfg = 0; cfg < ws::kMultiMenu; ++cfg) {
+    group_off[cfg] = nchunks;
+    for (size_t i = 0; i < sl.reqs.size(); ++i) {
+      if (sl.h_items[i].cfg != cfg) continue;
+      for (u64 st = 0; st < sl.h_items[i].a.n; st += ws::kMultiChunk) {
         ws::MultiChunk c;
         c.item = (u32)i;
         c.pad = 0;
@@ -229,18 +246,19 @@ bool launch_slot(ws_server* sv, Slot& sl) {
         sl.h_chunks[nchunks++] = c;
       }
     }
-    off += n;
   }
+  group_off[ws::kMultiMenu] = nchunks;
   if (ok && nchunks) {
     ok = cudaMemcpyAsync(sl.d_items, sl.h_items, sl.reqs.size() * sizeof(ws::MultiItem), cudaMemcpyHostToDevice,
                          s) == cudaSuccess &&
          cudaMemcpyAsync(sl.d_chunks, sl.h_chunks, nchunks * sizeof(ws::MultiChunk), cudaMemcpyHostToDevice, s) ==
              cudaSuccess &&
-         cudaMemsetAsync(sl.d_ticket, 0, sizeof(u32), s) == cudaSuccess;
-    if (ok) {
-      const u64 g = std::min<u64>((u64)sv->occ * (u64)sv->num_sms, nchunks);
-      ws::multi_kernel<<<(unsigned)g, ws::kThreads, 0, s>>>(sl.d_items, sl.d_chunks, (u32)nchunks, sl.d_ticket);
-      ok = cudaGetLastError() == cudaSuccess;
+         cudaMemsetAsync(sl.d_ticket, 0, ws::kMultiMenu * sizeof(u32), s) == cudaSuccess;
+    for (int cfg = 0; cfg < ws::kMultiMenu && ok; ++cfg) {
+      const u64 n_c = group_off[cfg + 1] - group_off[cfg];
+      if (!n_c) continue;
+      ws::MultiGroup g{sl.d_items, sl.d_chunks + group_off[cfg], nullptr, 0, 0, (u32)n_c, sl.d_ticket + cfg};
+      ok = ws::launch_multi(cfg, ws::KIND_MIXED, g, s, sv->num_sms) == cudaSuccess;
     }
   }
   for (size_t k = 0; k < fallback.size() && ok; ++k) {
@@ -352,13 +370,11 @@ ws_status ws_server_create(const ws_server_config* cfg, ws_server** out) {
   if (!sv) return WS_ERR_OOM;
   sv->cfg = c;
   sv->device = dev;
-  if (cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sv->occ, ws::multi_kernel, ws::kThreads, 0) != cudaSuccess) {
+  if (cudaDeviceGetAttribute(&sv->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
     note_cuda(cudaGetLastError(), "server setup");
     delete sv;
     return WS_ERR_CUDA;
   }
-  if (sv->occ < 1) sv->occ = 1;
   sv->max_chunks = c.max_batch_ops / ws::kMultiChunk + c.max_batch_reqs + 1;
   sv->slots.resize((size_t)c.max_inflight);
   for (Slot& sl : sv->slots) {
@@ -368,6 +384,16 @@ ws_status ws_server_create(const ws_server_config* cfg, ws_server** out) {
       return WS_ERR_OOM;
     }
   }
+  // Tables grow through the stream-ordered allocator.  With the default
+  // release threshold (0) the pool hands freed memory back to the driver at
+  // every synchronisation, and the next multi-gigabyte growth has to map it
+  // again inside a launch slot; keep freed memory pooled instead.
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
   sv->worker = std::thread(worker_main, sv);
   *out = sv;
   return WS_OK;
@@ -378,7 +404,7 @@ ws_status ws_server_add_table(ws_server* sv, uint64_t capacity, ws_scheme scheme
   if (!sv || !id) return WS_ERR_INVALID;
   DeviceGuard guard(sv->device);
   size_t fr = 0, tot = 0;
-  WS_CUDA(cudaMemGetInfo(&fr, &tot));
+  if (!avail_bytes(sv->device, &fr, &tot)) return WS_ERR_CUDA;
   const double bytes = (double)capacity * 1.25 * (16.0 + (metadata ? 2.0 : 0.0));  // up to pow2 rounding
   if ((double)fr - bytes < sv->cfg.hbm_headroom * (double)tot) return WS_ERR_OOM;  // not admitted
   ws_config c;
