@@ -191,13 +191,14 @@ def peak_gbs():
 
 
 def kernel_source_hash():
-    """Hash of the CUDA sources: recorded DRAM traffic is valid only for the
-    kernels it was measured on."""
+    """Hash of the sources of the single-table kernels the default line runs
+    (device header, kernel templates, instantiation units): recorded DRAM
+    traffic is valid only for the kernels it was measured on."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2509_16407_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f in ("ws_device.cuh", "ws_kernels.cuh") or (f.startswith("ws_inst_") and f.endswith(".cu")):
             h.update(f.encode())
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(fh.read())

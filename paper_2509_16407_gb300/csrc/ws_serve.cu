@@ -18,6 +18,7 @@
 // when memory admits it.  Plain mode (one request per launch, one launch at a
 // time, single-table kernel) is the per-request baseline.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -80,12 +81,20 @@ struct ws_server {
   int device = 0, num_sms = 0;
   u64 max_chunks = 0;
   std::vector<STable> tables;
-  std::vector<SReq> reqs;  // index = id
+  std::vector<SReq> reqs;  // index = id (worker-owned once moved in from the inbox)
   std::vector<Slot> slots;
   std::vector<ws_completion> done;
-  uint64_t n_submitted = 0, n_completed = 0, n_launches = 0, n_grows = 0;
+  uint64_t n_completed = 0, n_launches = 0, n_grows = 0;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
+  std::condition_variable cv_done;
+  // Submissions go to an inbox under their own mutex, so a submit never waits
+  // for the worker, which holds `mu` while it issues a slot's CUDA calls.
+  std::mutex in_mu;
+  std::condition_variable cv_in;  // wakes the worker: new requests or `wake`
+  std::vector<SReq> inbox;
+  bool wake = false;
+  std::atomic<uint64_t> n_submitted{0};
+  std::atomic<uint32_t> n_tables{0};
   std::thread worker;
   bool stop = false;
   bool paused = false;
@@ -313,11 +322,41 @@ void finish_slot(ws_server* sv, Slot& sl) {
   sl.busy = false;
 }
 
+void wake_worker(ws_server* sv) {
+  {
+    std::lock_guard<std::mutex> il(sv->in_mu);
+    sv->wake = true;
+  }
+  sv->cv_in.notify_one();
+}
+
+// Moves submitted requests into the per-table queues (worker, `mu` held);
+// counts each request's writes (growth estimate) and erases here, off the
+// submitting thread.
+void take_inbox(ws_server* sv) {
+  std::vector<SReq> in;
+  {
+    std::lock_guard<std::mutex> il(sv->in_mu);
+    in.swap(sv->inbox);
+    sv->wake = false;
+  }
+  for (SReq& q : in) {
+    for (uint64_t i = 0; i < q.r.n; ++i) {
+      const uint8_t o = q.r.ops[i];
+      q.n_write += (o >= WS_MX_INSERT && o <= WS_MX_REPLACE) ? 1 : 0;
+      q.has_erase |= (o == WS_MX_ERASE);
+    }
+    sv->tables[q.r.table].pending.push_back(q.id);
+    sv->reqs.push_back(q);  // ids are handed out in inbox order: index == id
+  }
+}
+
 void worker_main(ws_server* sv) {
   DeviceGuard guard(sv->device);
   cudaSetDevice(sv->device);
   std::unique_lock<std::mutex> lk(sv->mu);
   for (;;) {
+    take_inbox(sv);
     bool progress = false;
     for (Slot& sl : sv->slots) {
       if (sl.busy && cudaEventQuery(sl.done) != cudaErrorNotReady) {
@@ -336,14 +375,17 @@ void worker_main(ws_server* sv) {
     bool any_busy = false, any_pending = false;
     for (const Slot& sl : sv->slots) any_busy |= sl.busy;
     for (const STable& t : sv->tables) any_pending |= !t.pending.empty();
-    if (sv->stop && !any_busy && !any_pending) break;
+    if (sv->stop && !any_busy && !any_pending && sv->reqs.size() == sv->n_submitted.load()) break;
     if (progress) continue;
-    if (any_busy) {
-      // launches in flight: look again shortly (new requests also wake us)
-      sv->cv_work.wait_for(lk, std::chrono::microseconds(20));
-    } else {
-      sv->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+    // launches in flight: look again shortly; idle: sleep until a request or
+    // a state change (pause, drain, stop) arrives
+    lk.unlock();
+    {
+      std::unique_lock<std::mutex> il(sv->in_mu);
+      const auto dur = any_busy ? std::chrono::microseconds(20) : std::chrono::microseconds(2000);
+      sv->cv_in.wait_for(il, dur, [&] { return !sv->inbox.empty() || sv->wake; });
     }
+    lk.lock();
   }
 }
 
@@ -421,6 +463,7 @@ ws_status ws_server_add_table(ws_server* sv, uint64_t capacity, ws_scheme scheme
   STable st;
   st.t = t;
   sv->tables.push_back(st);
+  sv->n_tables.store((uint32_t)sv->tables.size());
   *id = (uint32_t)(sv->tables.size() - 1);
   return WS_OK;
 }
@@ -428,22 +471,18 @@ ws_status ws_server_add_table(ws_server* sv, uint64_t capacity, ws_scheme scheme
 ws_status ws_server_submit(ws_server* sv, const ws_request* r, uint64_t* id) {
   if (!sv || !r || (r->n && (!r->ops || !r->keys))) return WS_ERR_INVALID;
   if (r->n > sv->cfg.max_batch_ops) return WS_ERR_INVALID;
+  if (r->table >= sv->n_tables.load()) return WS_ERR_INVALID;
   SReq q;
   q.r = *r;
   q.t_submit = now_s();
-  for (uint64_t i = 0; i < r->n; ++i) {
-    const uint8_t o = r->ops[i];
-    q.n_write += (o >= WS_MX_INSERT && o <= WS_MX_REPLACE) ? 1 : 0;
-    q.has_erase |= (o == WS_MX_ERASE);
+  {
+    std::lock_guard<std::mutex> il(sv->in_mu);
+    q.id = sv->n_submitted.load();
+    sv->inbox.push_back(q);
+    sv->n_submitted.store(q.id + 1);
   }
-  std::lock_guard<std::mutex> lk(sv->mu);
-  if (r->table >= sv->tables.size()) return WS_ERR_INVALID;
-  q.id = sv->reqs.size();
-  sv->reqs.push_back(q);
-  sv->tables[r->table].pending.push_back(q.id);
-  ++sv->n_submitted;
+  sv->cv_in.notify_one();
   if (id) *id = q.id;
-  sv->cv_work.notify_one();
   return WS_OK;
 }
 
@@ -461,9 +500,11 @@ ws_status ws_server_poll(ws_server* sv, ws_completion* out, uint64_t max, uint64
 
 ws_status ws_server_pause(ws_server* sv, int paused) {
   if (!sv) return WS_ERR_INVALID;
-  std::lock_guard<std::mutex> lk(sv->mu);
-  sv->paused = paused != 0;
-  sv->cv_work.notify_one();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->paused = paused != 0;
+  }
+  wake_worker(sv);
   return WS_OK;
 }
 
@@ -471,8 +512,10 @@ ws_status ws_server_drain(ws_server* sv) {
   if (!sv) return WS_ERR_INVALID;
   std::unique_lock<std::mutex> lk(sv->mu);
   sv->paused = false;  // draining a paused server would wait forever
-  sv->cv_work.notify_one();
-  sv->cv_done.wait(lk, [&] { return sv->n_completed == sv->n_submitted; });
+  lk.unlock();
+  wake_worker(sv);
+  lk.lock();
+  sv->cv_done.wait(lk, [&] { return sv->n_completed == sv->n_submitted.load(); });
   return sv->error ? (ws_status)sv->error : WS_OK;
 }
 
@@ -488,7 +531,7 @@ ws_status ws_server_stats(ws_server* sv, uint64_t* submitted, uint64_t* complete
                           uint64_t* grows) {
   if (!sv) return WS_ERR_INVALID;
   std::lock_guard<std::mutex> lk(sv->mu);
-  if (submitted) *submitted = sv->n_submitted;
+  if (submitted) *submitted = sv->n_submitted.load();
   if (completed) *completed = sv->n_completed;
   if (launches) *launches = sv->n_launches;
   if (grows) *grows = sv->n_grows;
@@ -500,8 +543,8 @@ ws_status ws_server_destroy(ws_server* sv) {
   {
     std::lock_guard<std::mutex> lk(sv->mu);
     sv->stop = true;
-    sv->cv_work.notify_one();
   }
+  wake_worker(sv);
   if (sv->worker.joinable()) sv->worker.join();
   {
     DeviceGuard guard(sv->device);
