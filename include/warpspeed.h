@@ -144,14 +144,15 @@ ws_status ws_set_tile(ws_table* t, int tile);
 ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
 
 /* Tuning options (affect speed only, never results).
- *  WS_OPT_PRELOAD (default 1): before a warp's tiles probe, each lane copies its
- *  op's first probe -- the first 128-byte line of the primary bucket, or with
- *  metadata the bucket's tag line and first tag-matching slot -- into shared
- *  memory with asynchronous copies, so 32 first probes per warp are in flight
- *  at once.  0 reads everything with plain loads. */
+ *  WS_OPT_PRELOAD (default 1): the lane path -- each lane follows its op's
+ *  probe sequence from bucket snapshots the warp copies into shared memory
+ *  with asynchronous copies (the 128-byte line of a plain bucket, or the tag
+ *  line and the first tag-matching slot), up to 32 probes per warp in flight
+ *  per wave.  0 serves every op with the cooperative tiles and plain loads. */
 /*  WS_OPT_PHASED (default 0): bulk-synchronous mode, the paper's "phased"
- *  tables of the concurrency-overhead benchmark (§6.2): probes use weak
- *  L1-cacheable loads and absent-key inserts take no lock.  Valid only for
+ *  tables of the concurrency-overhead benchmark (§6.2): query probes use weak
+ *  L1-cacheable loads and absent-key inserts take no lock (inserts and erases
+ *  still read through L2: they must see each other's claims).  Valid only for
  *  calls whose keys are distinct and whose probed slots nothing else writes
  *  during the call (e.g. a pure query batch, or inserts of distinct new
  *  keys); otherwise results are undefined. */

@@ -145,7 +145,7 @@ class Table:
         _check(lib().ws_set_spin_limit(self._h, int(spins)), "ws_set_spin_limit")
 
     def set_preload(self, on: bool):
-        """First-probe preload into shared memory (on by default)."""
+        """The lane path with shared-memory bucket snapshots (on by default); off: tiles only."""
         _check(lib().ws_set_option(self._h, 1, int(bool(on))), "ws_set_option")
 
     def set_phased(self, on: bool):

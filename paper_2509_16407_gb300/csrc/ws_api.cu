@@ -28,7 +28,7 @@ constexpr u64 kSeed2 = 0x13198a2e03707344ull;
 constexpr uint32_t kDefaultProbe = 80;
 constexpr uint32_t kDefaultSpin = 1u << 16;  // attempts; each costs a probe + <= 1 us back-off
 constexpr u64 kStageOps = 1ull << 22;  // ops per staging chunk (host-buffer path)
-constexpr int kDefaultPreload = 1;  // first-probe preload (see WS_OPT_PRELOAD)
+constexpr int kDefaultPreload = 1;  // the lane path (see WS_OPT_PRELOAD)
 
 }  // namespace
 

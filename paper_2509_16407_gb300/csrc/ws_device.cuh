@@ -59,7 +59,7 @@ struct TableView {
   u32 pmax;       // double hashing: buckets a probe sequence may visit (<= nb)
   u32 spin_limit; // lock attempts before giving up
   int shortcut;   // P2: no erase ever ran, so the primary-fill shortcut is exact
-  int preload;    // stage each op's first probe into shared memory with async copies (1) or not (0)
+  int preload;    // the lane path with cp.async snapshots (1), or every op to the tiles (0)
   int phased;     // bulk-synchronous mode: weak cacheable probe loads, no locks (see WS_OPT_PHASED)
   int lane_waves; // double hashing: buckets the lane path checks before the tiles (0 = default)
   int stream;     // single-table launches: streaming lanes (1) or 32-op chunks (0); see WS_OPT_STREAM
@@ -117,19 +117,6 @@ __device__ __forceinline__ void ld_slot(const Slot* p, u64& k, u64& v) {
       : "memory");
 }
 
-// The pair store of a metadata claim.  It follows the tag CAS, which has
-// acquire semantics, so it cannot be performed before the claim; no earlier
-// write of the thread needs to be published with it, so no release (a
-// release store waits for all of them).
-__device__ __forceinline__ void st_slot_relaxed(Slot* p, u64 k, u64 v) {
-  asm volatile(
-      "{\n\t.reg .b128 t;\n\t"
-      "mov.b128 t, {%1, %2};\n\t"
-      "st.relaxed.gpu.global.b128 [%0], t;\n\t}" ::"l"(p),
-      "l"(k), "l"(v)
-      : "memory");
-}
-
 // Weak (L1-cacheable) loads for the bulk-synchronous mode: valid only while
 // nothing writes what they read during the launch.
 __device__ __forceinline__ void ld_slot_weak(const Slot* p, u64& k, u64& v) {
@@ -165,6 +152,19 @@ __device__ __forceinline__ u16 cas_tag(u16* p, u16 expect, u16 desired) {
                : "l"(p), "h"(expect), "h"(desired)
                : "memory");
   return old;
+}
+
+// The pair store of a metadata claim.  It follows the tag CAS, which has
+// acquire semantics, so it cannot be performed before the claim; no earlier
+// write of the thread needs to be published with it, so no release (a
+// release store waits for all of them).
+__device__ __forceinline__ void st_slot_relaxed(Slot* p, u64 k, u64 v) {
+  asm volatile(
+      "{\n\t.reg .b128 t;\n\t"
+      "mov.b128 t, {%1, %2};\n\t"
+      "st.relaxed.gpu.global.b128 [%0], t;\n\t}" ::"l"(p),
+      "l"(k), "l"(v)
+      : "memory");
 }
 
 __device__ __forceinline__ void st_tag_release(u16* p, u16 v) {
@@ -204,9 +204,9 @@ __device__ __forceinline__ void st_u64_relaxed(u64* p, u64 v) {
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Asynchronous 16-byte global -> shared copy through L2 (cp.async.cg): the
-// first-probe snapshot of an op lands in shared memory without holding
-// registers, so a warp keeps all 32 of its ops' first probes in flight.
+// Asynchronous 16-byte global -> shared copy through L2 (cp.async.cg): an
+// op's bucket snapshot lands in shared memory without holding registers, so
+// a warp keeps all 32 of its ops' probes of a wave in flight.
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   const u32 d = (u32)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");

@@ -1,13 +1,16 @@
-// ws_kernels.cuh -- tile-cooperative batch kernels for bucketed open addressing.
+// ws_kernels.cuh -- batch kernels for bucketed open addressing.
 //
-// One cooperative tile of T lanes (T in {4, 8, 16, 32}, densely packed in a
-// warp, §3.2 / §5) serves one operation at a time.  A bucket of B slots
-// (16 B each) is read in steps of T consecutive slots, so for B = 8, T = 8 a
-// step is one coalesced 128-byte line per tile; for T > B one step covers
-// T/B buckets at once (the next buckets of a double-hashing sequence, or
-// both choices of a two-choice key).  Key matches, empty slots and free
-// slots are found with warp votes over the tile, so every decision is the
-// same on all lanes of a tile.
+// Two levels serve an op.  The lane path: each lane owns one op and follows
+// its probe sequence one bucket (or one 128-byte line) per wave, from a
+// snapshot that the warp copies into shared memory with cp.async -- four ops'
+// lines per copy instruction, so up to 32 probes of a warp are in flight per
+// wave.  Single-table calls run "streaming lanes": a warp serves a
+// contiguous share of the batch and a lane takes the next op as soon as its
+// op settles.  What a lane cannot settle alone goes to cooperative tiles of
+// T lanes (T in {4, 8, 16, 32}, §3.2 / §5), which read a bucket in steps of
+// T consecutive 16-byte slots and decide with warp votes, identically on all
+// lanes of the tile: several tag matches, a lost CAS, an insert without the
+// lock, the probe-count kernel.
 //
 // Probe schemes (§2.2):
 //   double hashing  b_i = (h1 + i * (h2 | 1)) mod nb, i < max_probe; a scan
@@ -16,33 +19,32 @@
 //                   insert goes to b_0 while it is below 3/4 full (the
 //                   "shortcut" of §2.2), otherwise to the less loaded bucket
 //                   (ties to b_0).
+//   iceberg         a front-yard bucket by single hashing, then two backyard
+//                   choices; a key goes to its front bucket while that has a
+//                   free slot.
 // Fingerprints (§4.3): with metadata, each 32-slot bucket has a 64-byte line
 // of 16-bit tags.  A probe reads the tag line, and only slots whose tag
 // matches are read and compared against the full key, so the result is exact.
 //
-// First-probe preload.  A tile resolves its ops one after another, so with
-// plain loads only 32/T probes of a warp are in flight.  Before the tiles
-// start, each lane therefore copies the first probe of "its" op of the
-// 32-op chunk -- the first 128-byte line of b_0, or with metadata the tag
-// line of b_0 and then the first slot whose tag matches -- into shared
-// memory with cp.async, so all 32 ops' first DRAM round trips overlap.  The
-// snapshot only stands in for the first read of a lock-free probe: a query
-// answer may come from it (queried keys are not written in the same call),
-// every write is a CAS against the current slot, and everything under a
-// lock is read afresh.
+// Snapshots stand in for lock-free reads only: a query answer may come from
+// one (queried keys are not written in the same call), every write is a CAS
+// against the current slot, and what decides an insert under a lock is read
+// after the lock was taken.
 //
 // Concurrency (§4.1, §4.2):
-//   * queries take no lock; each slot is read with one 128-bit load;
-//   * an upsert first probes lock-free; a present key is updated in place
-//     with a 64-bit atomic (stability, §2.1: keys never move);
+//   * queries take no lock; each slot is read as one 16-byte pair;
+//   * a present key is updated in place with a 64-bit atomic and no lock
+//     (stability, §2.1: keys never move);
 //   * plain insert / upsert calls on double-hashing tables need no lock at all
 //     (no erase runs in the same call, see do_upsert);
-//   * otherwise an absent key takes the lock bit of its primary bucket b_0
-//     (one bit per bucket in an external array), re-scans, and claims a free
-//     slot with one 128-bit CAS that publishes key and value together
-//     (metadata tables: a 16-bit CAS on the tag, then a 128-bit release store
-//     of the pair).  The lock makes same-key inserters agree on one location
-//     (the adversarial case of Fig. 2);
+//   * otherwise an absent key is inserted under the lock bit of its primary
+//     bucket b_0 (one bit per bucket in an external array; iceberg: the front
+//     bucket): insert-if-unique ops take it before probing, add / max /
+//     replace only once the key is proven absent.  The holder re-reads and
+//     claims a free slot with one 128-bit CAS that publishes key and value
+//     together (metadata tables: a 16-bit CAS on the tag, then a 128-bit
+//     store of the pair).  The lock makes same-key inserters agree on one location (the
+//     adversarial case of Fig. 2);
 //   * erase swaps the pair for {TOMB, 0} with a 128-bit CAS (then the tag
 //     becomes TOMB).  A tombstone never turns back into EMPTY, which keeps
 //     every early-exit rule valid.
@@ -162,7 +164,7 @@ struct TileOps {
   }
 
   // ----------------------------------------------------------------------
-  // First-probe preload (one lane per op; see the file comment)
+  // Lane snapshots (one lane per op; see the file comment)
   // ----------------------------------------------------------------------
   // Metadata second copy of a wave: the first slot of bucket b whose tag
   // matches K, for op j.
@@ -441,8 +443,8 @@ struct TileOps {
   // The snapshot's candidate (same shared value on every lane) stands in for
   // the first read when it is that slot.  With WAIT (lock-free inserts, where
   // no erase runs concurrently) a slot whose tag is claimed but whose pair is
-  // not stored yet (key EMPTY/TOMB) is re-read until the claimer's release
-  // store lands, so a same-key inserter cannot miss a copy being written.
+  // not stored yet (key EMPTY/TOMB) is re-read until the claimer's pair store
+  // lands, so a same-key inserter cannot miss a copy being written.
   // *stuck reports a wait that ran out.
   template <bool WAIT = false, bool COUNT = false>
   __device__ static __forceinline__ bool verify(const TableView& tv, const TileCtx<T>& c, u64 b, unsigned mm,
@@ -733,7 +735,7 @@ struct TileOps {
 
   // ----------------------------------------------------------------------
   // Operations (tile-uniform control flow; results valid on every lane).
-  // pre: the op's first-probe snapshot, or null.
+  // pre: the op's snapshot of b_0, or null.
   // ----------------------------------------------------------------------
   __device__ static u8 do_query(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, PreRef pre,
                                 u64& out) {
@@ -764,8 +766,15 @@ struct TileOps {
   // LOCKFREE: the caller guarantees that no erase runs in the same launch (a
   // plain insert / upsert call is one phase).
   template <bool LOCKFREE>
-  __device__ static u8 do_upsert(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, u64 V, int op,
+  // Writes read the table through L2 even in bulk-synchronous mode: the
+  // call's other inserts write the slots they probe, and a lost claim must
+  // see the winner (weak, L1-cacheable loads could return the stale line on
+  // every retry).  `tv` keeps the mode for the lock decisions.
+  __device__ static u8 do_upsert(const TableView& tv_in, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, u64 V, int op,
                                  PreRef pre, int& dcount) {
+    TableView tv = tv_in;
+    const bool phased = tv.phased != 0;
+    tv.phased = 0;
     if (is_sentinel(K)) return ST_BADKEY;
     if (LOCKFREE && SCHEME == SCHEME_DOUBLE) {
       // Without erases, free slots only disappear, so every inserter of K
@@ -806,7 +815,7 @@ struct TileOps {
     // a batch's many copies of a hot key from queueing on one lock bit.
     const u64 b0 = bucket(tv, h1, h2, 0);
     // bulk-synchronous mode: distinct keys per call, nothing to serialise
-    for (u32 tries = 0, ns = 0; !tv.phased;) {
+    for (u32 tries = 0, ns = 0; !phased;) {
       if (try_lock(tv, c, b0)) break;
       const Hit again = find(tv, c, K, h1, h2, no_pre());
       if (again.found) {
@@ -834,12 +843,14 @@ struct TileOps {
         break;
       }
     }
-    if (!tv.phased) unlock(tv, c, b0, st == ST_INSERTED);
+    if (!phased) unlock(tv, c, b0, st == ST_INSERTED);
     return st;
   }
 
-  __device__ static u8 do_erase(const TableView& tv, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, PreRef pre,
+  __device__ static u8 do_erase(const TableView& tv_in, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, PreRef pre,
                                 u64& out, int& dcount) {
+    TableView tv = tv_in;  // through L2, as for do_upsert
+    tv.phased = 0;
     out = 0;
     if (is_sentinel(K)) return ST_BADKEY;
     for (int attempt = 0; attempt < 256; ++attempt) {
