@@ -166,24 +166,51 @@ struct TileOps {
   // ----------------------------------------------------------------------
   // Lane snapshots (one lane per op; see the file comment)
   // ----------------------------------------------------------------------
-  // Metadata second copy of a wave: the first slot of bucket b whose tag
-  // matches K, for op j.
-  __device__ static __forceinline__ void preload_candidate(const TableView& tv, u64 K, u64 b0, PreWarp* pw, int j) {
-    const u16 kt = key_tag(K);
-    int q = -1;
+  // Summary of a snapshot's 32 tags, packed in one word (it stays live
+  // across the candidate copy): bits 0-5 first tag equal to the key's (63:
+  // none), 6-11 number of such tags, 12-17 first free tag (EMPTY or TOMB;
+  // 63: none), 18 that free tag is EMPTY, 19 some tag is EMPTY, 20-25
+  // occupied tags.  Four tags per 64-bit word are tested at once: a field's
+  // bit 15 of zero16(x) is set exactly when the field of x is zero.
+  static constexpr u32 kTsNone = 63u;
+  __device__ static __forceinline__ u64 zero16(u64 x) {
+    constexpr u64 lo = 0x7fff7fff7fff7fffull, hi = 0x8000800080008000ull;
+    return ~(((x & lo) + lo) | x) & hi;  // (f & 0x7fff) + 0x7fff <= 0xfffe: no carry between fields
+  }
+  __device__ static __forceinline__ u32 tag_scan(const PreWarp* pw, int j, u16 kt) {
+    const u64 k4 = (u64)kt * 0x0001000100010001ull;
+    u32 first = kTsNone, ffree = kTsNone, nmatch = 0, nfree = 0, fempty = 0, empty = 0;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const u16* t = reinterpret_cast<const u16*>(&pw->at(j, r));
-#pragma unroll
-      for (int h = 0; h < 8; ++h)
-        if (q < 0 && t[h] == kt) q = 8 * r + h;
+    for (int i = 0; i < 8; ++i) {
+      const u64 x = reinterpret_cast<const u64*>(&pw->at(j, i >> 1))[i & 1];
+      const u64 me = zero16(x ^ k4);                    // tag == kt (kt >= 2)
+      const u64 mf = zero16(x & 0xfffefffefffefffeull);  // tag < 2: EMPTY or TOMB
+      const u64 mz = zero16(x);                          // tag == EMPTY
+      nmatch += (u32)__popcll(me);
+      nfree += (u32)__popcll(mf);
+      empty |= (mz != 0);
+      if (first == kTsNone && me) first = 4u * i + (u32)(__ffsll((long long)me) >> 4) - 1u;
+      if (ffree == kTsNone && mf) {
+        const u32 h = (u32)(__ffsll((long long)mf) >> 4) - 1u;
+        ffree = 4u * i + h;
+        fempty = (u32)((mz >> (16u * h + 15u)) & 1ull);
+      }
     }
-    if (q >= 0) {
+    return first | (nmatch << 6) | (ffree << 12) | (fempty << 18) | (empty << 19) | ((32u - nfree) << 20);
+  }
+
+  // Metadata second copy of a wave: the first slot of bucket b whose tag
+  // matches K, for op j.  Returns the snapshot's tag summary.
+  __device__ static __forceinline__ u32 preload_candidate(const TableView& tv, u64 K, u64 b0, PreWarp* pw, int j) {
+    const u32 ts = tag_scan(pw, j, key_tag(K));
+    const u32 q = ts & 63u;
+    if (q != kTsNone) {
       ptx::cp_async16(&pw->at(j, 4), tv.slots + b0 * 32 + (u64)q);
       pw->at(j, 5).key = b0 * 32 + (u64)q;
     } else {
       pw->at(j, 5).key = kNoCand;
     }
+    return ts;
   }
 
   // ----------------------------------------------------------------------
@@ -901,7 +928,8 @@ struct TileOps {
     bool unsure;     // metadata: a tag match that the snapshot cannot settle
   };
 
-  __device__ static __forceinline__ Snap snap_of(PreRef p, u64 K) {
+  // ts: the tag summary of the snapshot (metadata tables; see tag_scan).
+  __device__ static __forceinline__ Snap snap_of(PreRef p, u64 K, u32 ts) {
     Snap sn;
     sn.hit = -1;
     sn.ffree = -1;
@@ -923,24 +951,11 @@ struct TileOps {
         sn.occ += fr ? 0u : 1u;
       }
     } else {
-      const u16 kt = key_tag(K);
-      int nmatch = 0;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {  // eight words of four tags, two per row
-        const u64 x = reinterpret_cast<const u64*>(p.tagrow(i >> 1))[i & 1];
-#pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          const u16 t = (u16)((x >> (16 * h)) & 0xffffu);
-          const int q = 4 * i + h;
-          nmatch += (t == kt);
-          if (t < 2 && sn.ffree < 0) {
-            sn.ffree = q;
-            sn.ffree_empty = (t == TAG_EMPTY);
-          }
-          sn.empty |= (t == TAG_EMPTY);
-          sn.occ += (t < 2) ? 0u : 1u;
-        }
-      }
+      const u32 nmatch = (ts >> 6) & 63u, ff = (ts >> 12) & 63u;
+      sn.ffree = ff == kTsNone ? -1 : (int)ff;
+      sn.ffree_empty = (ts >> 18) & 1u;
+      sn.empty = (ts >> 19) & 1u;
+      sn.occ = (ts >> 20) & 63u;
       if (nmatch > 0) {
         const u64 ck = p.cand().key;
         if (ck == K)
@@ -986,6 +1001,7 @@ struct TileOps {
     u64 f1_v;     // two-choice by lines: observed value of b_1's first free slot
     u32 cur_occ;  // two-choice by lines: occupied slots of the current bucket so far
     u32 next_w;   // two-choice by lines: the wave to run next
+    u32 tsum;     // metadata: tag summary of the current snapshot (tag_scan)
   };
 
   // Two-choice tables whose buckets are wider than a snapshot line: wave w
@@ -1003,7 +1019,7 @@ struct TileOps {
                                                         int& dcount, bool& fresh) {
     const u32 c = w / kLinesPerBucket, l = w % kLinesPerBucket;
     const u64 line0 = bw * B + (u64)l * PRE_SLOTS;
-    const Snap sn = snap_of(p, K);
+    const Snap sn = snap_of(p, K, 0u);
     if (sn.hit >= 0) {
       const u64 idx = line0 + (u64)sn.hit;
       const u64 v = p.slot(sn.hit).val;
@@ -1079,7 +1095,7 @@ struct TileOps {
   __device__ static __forceinline__ int lane_wave(const TableView& tv, PreRef p, u64 K, u64 V, int op, int opk,
                                                   u32 w, u64 bw, LaneState& ls, u64& out, u8& st, int& dcount,
                                                   bool& fresh) {
-    const Snap sn = snap_of(p, K);
+    const Snap sn = snap_of(p, K, ls.tsum);
     if (sn.unsure) return -1;
     if (sn.hit >= 0) {
       u64 idx, v;
@@ -1429,6 +1445,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
   ls.ff_idx = ls.ff_k = ls.ff_v = 0;
   ls.occ0 = ls.occ1 = 0;
   ls.f1_set = false;
+  ls.tsum = 0;
   ls.f1_idx = ls.f1_k = 0;
   // waves: a double-hashing sequence is followed for lane_waves buckets
   // (default 4); the other schemes have 2 or 3 candidate buckets
@@ -1459,7 +1476,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     ptx::cp_async_wait_all();
     __syncwarp();
     if (META) {
-      if (want) Ops::preload_candidate(tv, K, sm.bw[lane], &sm.pre, lane);
+      if (want) ls.tsum = Ops::preload_candidate(tv, K, sm.bw[lane], &sm.pre, lane);
       ptx::cp_async_wait_all();
       __syncwarp();
     }
@@ -1614,6 +1631,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           ls.ff_idx = ls.ff_k = ls.ff_v = 0;
           ls.occ0 = ls.occ1 = ls.cur_occ = ls.next_w = 0;
           ls.f1_set = false;
+          ls.tsum = 0;
           ls.f1_idx = ls.f1_k = ls.f1_v = 0;
           locked = false;
           if (!lane_path) {
@@ -1654,7 +1672,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
       ptx::cp_async_wait_all();
       __syncwarp();
       if (META) {
-        if (state == L_ACTIVE) Ops::preload_candidate(tv, sm.key[lane], sm.bw[lane], &sm.pre, lane);
+        if (state == L_ACTIVE) ls.tsum = Ops::preload_candidate(tv, sm.key[lane], sm.bw[lane], &sm.pre, lane);
         ptx::cp_async_wait_all();
         __syncwarp();
       }
@@ -1686,6 +1704,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           ls.ff_idx = ls.ff_k = ls.ff_v = 0;
           ls.occ0 = ls.occ1 = ls.cur_occ = ls.next_w = 0;
           ls.f1_set = false;
+          ls.tsum = 0;
           ls.f1_idx = ls.f1_k = ls.f1_v = 0;
         } else if (r < 0 || w + 1 >= cap) {
           state = L_PARKED;
