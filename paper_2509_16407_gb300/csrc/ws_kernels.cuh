@@ -177,8 +177,36 @@ struct TileOps {
     constexpr u64 lo = 0x7fff7fff7fff7fffull, hi = 0x8000800080008000ull;
     return ~(((x & lo) + lo) | x) & hi;  // (f & 0x7fff) + 0x7fff <= 0xfffe: no carry between fields
   }
+  //
+  // FULL = false (ops that claim no slot: queries, erases, updates probing
+  // without the lock) scans only for tags equal to K's.  EMPTY slots form a
+  // suffix of a bucket (every claim takes the bucket's first free slot), so
+  // tag 31 tells whether the bucket has one; and in a table that never saw
+  // an erase (no tombstones: the only case the two-choice shortcut runs),
+  // occupancy is below the 3/4 threshold exactly when tag 3B/4 - 1 is EMPTY.
+  // Occupancy is then reported only as FILL_SHORTCUT - 1 (below) or
+  // FILL_SHORTCUT (not below), and no free tag is reported.
+  template <bool FULL>
   __device__ static __forceinline__ u32 tag_scan(const PreWarp* pw, int j, u16 kt) {
     const u64 k4 = (u64)kt * 0x0001000100010001ull;
+    if constexpr (!FULL) {
+      u64 any = 0;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) any |= zero16(reinterpret_cast<const u64*>(&pw->at(j, i >> 1))[i & 1] ^ k4);
+      u32 first = kTsNone, nmatch = 0;
+      if (any) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const u64 me = zero16(reinterpret_cast<const u64*>(&pw->at(j, i >> 1))[i & 1] ^ k4);
+          nmatch += (u32)__popcll(me);
+          if (first == kTsNone && me) first = 4u * i + (u32)(__ffsll((long long)me) >> 4) - 1u;
+        }
+      }
+      const u16* t = reinterpret_cast<const u16*>(&pw->at(j, 0));
+      const u32 empty = t[31] == TAG_EMPTY;
+      const u32 occ = (t[FILL_SHORTCUT - 1] == TAG_EMPTY) ? FILL_SHORTCUT - 1 : FILL_SHORTCUT;
+      return first | (nmatch << 6) | (kTsNone << 12) | (empty << 19) | (occ << 20);
+    }
     u32 first = kTsNone, ffree = kTsNone, nmatch = 0, nfree = 0, fempty = 0, empty = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -201,8 +229,9 @@ struct TileOps {
 
   // Metadata second copy of a wave: the first slot of bucket b whose tag
   // matches K, for op j.  Returns the snapshot's tag summary.
+  template <bool FULL>
   __device__ static __forceinline__ u32 preload_candidate(const TableView& tv, u64 K, u64 b0, PreWarp* pw, int j) {
-    const u32 ts = tag_scan(pw, j, key_tag(K));
+    const u32 ts = tag_scan<FULL>(pw, j, key_tag(K));
     const u32 q = ts & 63u;
     if (q != kTsNone) {
       ptx::cp_async16(&pw->at(j, 4), tv.slots + b0 * 32 + (u64)q);
@@ -1476,7 +1505,11 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     ptx::cp_async_wait_all();
     __syncwarp();
     if (META) {
-      if (want) ls.tsum = Ops::preload_candidate(tv, K, sm.bw[lane], &sm.pre, lane);
+      // a full tag scan only when some lane of the warp may claim a slot
+      const bool full = (KIND != KIND_QUERY && KIND != KIND_ERASE) &&
+                        __any_sync(0xffffffffu, want && (opk == Ops::LW_INSERT_FREE || opk == Ops::LW_INSERT_LOCKED));
+      if (want) ls.tsum = full ? Ops::template preload_candidate<true>(tv, K, sm.bw[lane], &sm.pre, lane)
+                               : Ops::template preload_candidate<false>(tv, K, sm.bw[lane], &sm.pre, lane);
       ptx::cp_async_wait_all();
       __syncwarp();
     }
@@ -1672,7 +1705,13 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
       ptx::cp_async_wait_all();
       __syncwarp();
       if (META) {
-        if (state == L_ACTIVE) ls.tsum = Ops::preload_candidate(tv, sm.key[lane], sm.bw[lane], &sm.pre, lane);
+        // a full tag scan only when some lane of the warp may claim a slot
+        const bool full =
+            (KIND != KIND_QUERY && KIND != KIND_ERASE) &&
+            __any_sync(kAll, state == L_ACTIVE && (opk == Ops::LW_INSERT_FREE || opk == Ops::LW_INSERT_LOCKED));
+        if (state == L_ACTIVE)
+          ls.tsum = full ? Ops::template preload_candidate<true>(tv, sm.key[lane], sm.bw[lane], &sm.pre, lane)
+                         : Ops::template preload_candidate<false>(tv, sm.key[lane], sm.bw[lane], &sm.pre, lane);
         ptx::cp_async_wait_all();
         __syncwarp();
       }
