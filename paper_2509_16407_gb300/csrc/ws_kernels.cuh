@@ -1482,49 +1482,80 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
                         : (SCHEME == SCHEME_DOUBLE) ? (tv.lane_waves > 0 ? (u32)tv.lane_waves : 4u)
                         : (SCHEME == SCHEME_ICEBERG) ? 3u
                                                      : 2u;
-  for (u32 w = 0; w < max_waves; ++w) {
-    const bool want = lane_ok && !done;
-    const unsigned wmask = __ballot_sync(0xffffffffu, want);
-    if (!wmask) break;
-    sm.bw[lane] = want ? Ops::bucket(tv, h1, h2, w) : 0;
-    __syncwarp();
-    if (META) {
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int j = i * 8 + (lane >> 2), part = lane & 3;
-        if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.tags + sm.bw[j] * 32 + 8 * part);
+  // Pass 0 follows every open op.  Pass 1 reads again, under b_0's lock, the
+  // ops whose keys proved absent without it (a lane that missed the lock, or
+  // an add / max / replace that probed lock-free): by then the lock's holder
+  // has usually finished, and the lane settles the op from L2-resident lines
+  // instead of handing it to a tile that would spin on the lock.
+  bool relock = false;
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      bool again = false;
+      if (relock) {
+        again = Ops::lane_lock(tv, b0);
+        if (again) {
+          locked = true;
+          opk = Ops::LW_INSERT_LOCKED;
+          ls.ff_set = false;
+          ls.ff_idx = ls.ff_k = ls.ff_v = 0;
+          ls.occ0 = ls.occ1 = 0;
+          ls.f1_set = false;
+          ls.tsum = 0;
+          ls.f1_idx = ls.f1_k = 0;
+        }
       }
-    } else {
-      constexpr int PS = Ops::PRE_SLOTS;  // 8 slots = 128 B per op
-#pragma unroll
-      for (int i = 0; i < PS; ++i) {
-        const int j = i * (32 / PS) + lane / PS, part = lane % PS;
-        if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.slots + sm.bw[j] * B + (u64)part);
-      }
+      if (!__any_sync(0xffffffffu, again)) break;
+      lane_ok = again;  // the other open ops (a sequence longer than the waves) go to the tiles
     }
-    ptx::cp_async_wait_all();
-    __syncwarp();
-    if (META) {
-      // a full tag scan only when some lane of the warp may claim a slot
-      const bool full = (KIND != KIND_QUERY && KIND != KIND_ERASE) &&
-                        __any_sync(0xffffffffu, want && (opk == Ops::LW_INSERT_FREE || opk == Ops::LW_INSERT_LOCKED));
-      if (want) ls.tsum = full ? Ops::template preload_candidate<true>(tv, K, sm.bw[lane], &sm.pre, lane)
-                               : Ops::template preload_candidate<false>(tv, K, sm.bw[lane], &sm.pre, lane);
+    for (u32 w = 0; w < max_waves; ++w) {
+      const bool want = lane_ok && !done;
+      const unsigned wmask = __ballot_sync(0xffffffffu, want);
+      if (!wmask) break;
+      sm.bw[lane] = want ? Ops::bucket(tv, h1, h2, w) : 0;
+      __syncwarp();
+      if (META) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int j = i * 8 + (lane >> 2), part = lane & 3;
+          if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.tags + sm.bw[j] * 32 + 8 * part);
+        }
+      } else {
+        constexpr int PS = Ops::PRE_SLOTS;  // 8 slots = 128 B per op
+#pragma unroll
+        for (int i = 0; i < PS; ++i) {
+          const int j = i * (32 / PS) + lane / PS, part = lane % PS;
+          if ((wmask >> j) & 1u) ptx::cp_async16(&sm.pre.at(j, part), tv.slots + sm.bw[j] * B + (u64)part);
+        }
+      }
       ptx::cp_async_wait_all();
       __syncwarp();
+      if (META) {
+        // a full tag scan only when some lane of the warp may claim a slot
+        const bool full = (KIND != KIND_QUERY && KIND != KIND_ERASE) &&
+                          __any_sync(0xffffffffu, want && (opk == Ops::LW_INSERT_FREE || opk == Ops::LW_INSERT_LOCKED));
+        if (want) ls.tsum = full ? Ops::template preload_candidate<true>(tv, K, sm.bw[lane], &sm.pre, lane)
+                                 : Ops::template preload_candidate<false>(tv, K, sm.bw[lane], &sm.pre, lane);
+        ptx::cp_async_wait_all();
+        __syncwarp();
+      }
+      if (want) {
+        snap_wave = (int)w;
+        const PreRef p{&sm.pre, lane};
+        const int r = Ops::lane_wave(tv, p, K, V, op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh);
+        if (r > 0) {
+          done = true;
+        } else if (r == -2 && kLaneLock && pass == 0 && !locked) {
+          relock = true;  // absent, and this op holds no lock
+          lane_ok = false;
+        } else if (r < 0) {
+          lane_ok = false;
+        }
+      }
+      __syncwarp();  // the next wave overwrites the snapshots
     }
-    if (want) {
-      snap_wave = (int)w;
-      const PreRef p{&sm.pre, lane};
-      const int r = Ops::lane_wave(tv, p, K, V, op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh);
-      if (r > 0)
-        done = true;
-      else if (r < 0)
-        lane_ok = false;
-    }
-    __syncwarp();  // the next wave overwrites the snapshots
+    if (locked && !tv.phased) Ops::lane_unlock(tv, b0, done && st == ST_INSERTED);  // after the claim
+    locked = false;
   }
-  if (locked && !tv.phased) Ops::lane_unlock(tv, b0, done && st == ST_INSERTED);  // after the claim
   // the tile path may reuse a snapshot only if it is still of b_0 and fresh
   const unsigned pre_mask = __ballot_sync(0xffffffffu, snap_wave == 0 && fresh);
   sm.out[lane] = out;
