@@ -168,70 +168,47 @@ struct TileOps {
   // ----------------------------------------------------------------------
   // Summary of a snapshot's 32 tags, packed in one word (it stays live
   // across the candidate copy): bits 0-5 first tag equal to the key's (63:
-  // none), 6-11 number of such tags, 12-17 first free tag (EMPTY or TOMB;
-  // 63: none), 18 that free tag is EMPTY, 19 some tag is EMPTY, 20-25
-  // occupied tags.  Four tags per 64-bit word are tested at once: a field's
-  // bit 15 of zero16(x) is set exactly when the field of x is zero.
+  // none), 6-11 number of such tags, 12-17 first free tag (always 63 here:
+  // see tag_free), 19 the bucket has an EMPTY slot, 20-25 occupancy as
+  // FILL_SHORTCUT - 1 (below the 3/4 threshold) or FILL_SHORTCUT (not below).
+  // Four tags per 64-bit word are tested at once: a field's bit 15 of
+  // zero16(x) is set exactly when the field of x is zero.  EMPTY slots form
+  // a suffix of a bucket (every claim takes the bucket's first free slot),
+  // so tag 31 tells whether the bucket has one; and in a table that never saw
+  // an erase (no tombstones: the only case the two-choice shortcut runs),
+  // occupancy is below 3/4 exactly when tag 3B/4 - 1 is EMPTY.
   static constexpr u32 kTsNone = 63u;
   __device__ static __forceinline__ u64 zero16(u64 x) {
     constexpr u64 lo = 0x7fff7fff7fff7fffull, hi = 0x8000800080008000ull;
     return ~(((x & lo) + lo) | x) & hi;  // (f & 0x7fff) + 0x7fff <= 0xfffe: no carry between fields
   }
-  //
-  // FULL = false (ops that claim no slot: queries, erases, updates probing
-  // without the lock) scans only for tags equal to K's.  EMPTY slots form a
-  // suffix of a bucket (every claim takes the bucket's first free slot), so
-  // tag 31 tells whether the bucket has one; and in a table that never saw
-  // an erase (no tombstones: the only case the two-choice shortcut runs),
-  // occupancy is below the 3/4 threshold exactly when tag 3B/4 - 1 is EMPTY.
-  // Occupancy is then reported only as FILL_SHORTCUT - 1 (below) or
-  // FILL_SHORTCUT (not below), and no free tag is reported.
-  template <bool FULL>
+  __device__ static __forceinline__ u64 tag_word(const PreWarp* pw, int j, int i) {
+    return reinterpret_cast<const u64*>(&pw->at(j, i >> 1))[i & 1];
+  }
   __device__ static __forceinline__ u32 tag_scan(const PreWarp* pw, int j, u16 kt) {
     const u64 k4 = (u64)kt * 0x0001000100010001ull;
-    if constexpr (!FULL) {
-      u64 any = 0;
+    u64 any = 0;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) any |= zero16(reinterpret_cast<const u64*>(&pw->at(j, i >> 1))[i & 1] ^ k4);
-      u32 first = kTsNone, nmatch = 0;
-      if (any) {
+    for (int i = 0; i < 8; ++i) any |= zero16(tag_word(pw, j, i) ^ k4);
+    u32 first = kTsNone, nmatch = 0;
+    if (any) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const u64 me = zero16(reinterpret_cast<const u64*>(&pw->at(j, i >> 1))[i & 1] ^ k4);
-          nmatch += (u32)__popcll(me);
-          if (first == kTsNone && me) first = 4u * i + (u32)(__ffsll((long long)me) >> 4) - 1u;
-        }
-      }
-      const u16* t = reinterpret_cast<const u16*>(&pw->at(j, 0));
-      const u32 empty = t[31] == TAG_EMPTY;
-      const u32 occ = (t[FILL_SHORTCUT - 1] == TAG_EMPTY) ? FILL_SHORTCUT - 1 : FILL_SHORTCUT;
-      return first | (nmatch << 6) | (kTsNone << 12) | (empty << 19) | (occ << 20);
-    }
-    u32 first = kTsNone, ffree = kTsNone, nmatch = 0, nfree = 0, fempty = 0, empty = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const u64 x = reinterpret_cast<const u64*>(&pw->at(j, i >> 1))[i & 1];
-      const u64 me = zero16(x ^ k4);                    // tag == kt (kt >= 2)
-      const u64 mf = zero16(x & 0xfffefffefffefffeull);  // tag < 2: EMPTY or TOMB
-      const u64 mz = zero16(x);                          // tag == EMPTY
-      nmatch += (u32)__popcll(me);
-      nfree += (u32)__popcll(mf);
-      empty |= (mz != 0);
-      if (first == kTsNone && me) first = 4u * i + (u32)(__ffsll((long long)me) >> 4) - 1u;
-      if (ffree == kTsNone && mf) {
-        const u32 h = (u32)(__ffsll((long long)mf) >> 4) - 1u;
-        ffree = 4u * i + h;
-        fempty = (u32)((mz >> (16u * h + 15u)) & 1ull);
+      for (int i = 0; i < 8; ++i) {
+        const u64 me = zero16(tag_word(pw, j, i) ^ k4);
+        nmatch += (u32)__popcll(me);
+        if (first == kTsNone && me) first = 4u * i + (u32)(__ffsll((long long)me) >> 4) - 1u;
       }
     }
-    return first | (nmatch << 6) | (ffree << 12) | (fempty << 18) | (empty << 19) | ((32u - nfree) << 20);
+    const u16* t = reinterpret_cast<const u16*>(&pw->at(j, 0));
+    const u32 empty = t[31] == TAG_EMPTY;
+    const u32 occ = (t[FILL_SHORTCUT - 1] == TAG_EMPTY) ? FILL_SHORTCUT - 1 : FILL_SHORTCUT;
+    return first | (nmatch << 6) | (kTsNone << 12) | (empty << 19) | (occ << 20);
   }
 
   // Metadata second copy of a wave: the first slot of bucket b whose tag
   // matches K, for op j.  Returns the snapshot's tag summary.
-  template <bool FULL>
   __device__ static __forceinline__ u32 preload_candidate(const TableView& tv, u64 K, u64 b0, PreWarp* pw, int j) {
-    const u32 ts = tag_scan<FULL>(pw, j, key_tag(K));
+    const u32 ts = tag_scan(pw, j, key_tag(K));
     const u32 q = ts & 63u;
     if (q != kTsNone) {
       ptx::cp_async16(&pw->at(j, 4), tv.slots + b0 * 32 + (u64)q);
@@ -996,6 +973,22 @@ struct TileOps {
     return sn;
   }
 
+  // The free tags of a metadata snapshot, for a lane that may claim a slot
+  // in it (the tag summary leaves them out): the first free tag (EMPTY or
+  // TOMB), whether it is EMPTY, and the exact occupancy.
+  __device__ static __forceinline__ void tag_free(PreRef p, Snap& sn) {
+    u32 ffree = kTsNone, nfree = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const u64 mf = zero16(tag_word(p.w, p.j, i) & 0xfffefffefffefffeull);  // tag < 2
+      nfree += (u32)__popcll(mf);
+      if (ffree == kTsNone && mf) ffree = 4u * i + (u32)(__ffsll((long long)mf) >> 4) - 1u;
+    }
+    sn.occ = 32u - nfree;
+    sn.ffree = ffree == kTsNone ? -1 : (int)ffree;
+    sn.ffree_empty = ffree != kTsNone && p.tagrow(0)[ffree] == TAG_EMPTY;
+  }
+
   // Slot index and pair of the snapshot hit.
   __device__ static __forceinline__ void hit_pair(PreRef p, const Snap& sn, u64 b0, u64& idx, u64& val) {
     if (META) {
@@ -1124,7 +1117,7 @@ struct TileOps {
   __device__ static __forceinline__ int lane_wave(const TableView& tv, PreRef p, u64 K, u64 V, int op, int opk,
                                                   u32 w, u64 bw, LaneState& ls, u64& out, u8& st, int& dcount,
                                                   bool& fresh) {
-    const Snap sn = snap_of(p, K, ls.tsum);
+    Snap sn = snap_of(p, K, ls.tsum);
     if (sn.unsure) return -1;
     if (sn.hit >= 0) {
       u64 idx, v;
@@ -1154,6 +1147,7 @@ struct TileOps {
     // slots form a suffix of the bucket)
     if (!META && PRE_SLOTS < B && !sn.empty) return -1;
     const bool ins = (opk == LW_INSERT_FREE || opk == LW_INSERT_LOCKED);
+    if (META && ins) tag_free(p, sn);  // K is not here: this lane may claim a slot
     if (SCHEME == SCHEME_P2 && w == 0) ls.occ0 = sn.occ;
     if (SCHEME == SCHEME_ICEBERG && w == 1) {
       ls.occ1 = sn.occ;
@@ -1530,11 +1524,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
       ptx::cp_async_wait_all();
       __syncwarp();
       if (META) {
-        // a full tag scan only when some lane of the warp may claim a slot
-        const bool full = (KIND != KIND_QUERY && KIND != KIND_ERASE) &&
-                          __any_sync(0xffffffffu, want && (opk == Ops::LW_INSERT_FREE || opk == Ops::LW_INSERT_LOCKED));
-        if (want) ls.tsum = full ? Ops::template preload_candidate<true>(tv, K, sm.bw[lane], &sm.pre, lane)
-                                 : Ops::template preload_candidate<false>(tv, K, sm.bw[lane], &sm.pre, lane);
+          if (want) ls.tsum = Ops::preload_candidate(tv, K, sm.bw[lane], &sm.pre, lane);
         ptx::cp_async_wait_all();
         __syncwarp();
       }
@@ -1736,13 +1726,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
       ptx::cp_async_wait_all();
       __syncwarp();
       if (META) {
-        // a full tag scan only when some lane of the warp may claim a slot
-        const bool full =
-            (KIND != KIND_QUERY && KIND != KIND_ERASE) &&
-            __any_sync(kAll, state == L_ACTIVE && (opk == Ops::LW_INSERT_FREE || opk == Ops::LW_INSERT_LOCKED));
-        if (state == L_ACTIVE)
-          ls.tsum = full ? Ops::template preload_candidate<true>(tv, sm.key[lane], sm.bw[lane], &sm.pre, lane)
-                         : Ops::template preload_candidate<false>(tv, sm.key[lane], sm.bw[lane], &sm.pre, lane);
+        if (state == L_ACTIVE) ls.tsum = Ops::preload_candidate(tv, sm.key[lane], sm.bw[lane], &sm.pre, lane);
         ptx::cp_async_wait_all();
         __syncwarp();
       }
