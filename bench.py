@@ -63,6 +63,9 @@ def parse():
                    help="config2 = the default line; batched = 1024 uneven tables in one graph launch")
     p.add_argument("--tables", type=int, default=1024)
     p.add_argument("--requests", type=int, default=600, help="serve: requests per run")
+    p.add_argument("--host-direct", type=int, default=1, choices=[0, 1, 2],
+                   help="e2e: page-locked host buffers staged (0), inputs read in place (1), "
+                        "inputs and results in place (2)")
     p.add_argument("--tiles", default="auto", choices=["auto", "paper", "4", "8", "16", "32"],
                    help="auto: per design, the tile size with the fastest step (measured before timing); "
                         "paper: each design's tile from the paper; a number: that tile for every design")
@@ -465,6 +468,8 @@ def bench_e2e(args, tables, keys_slice, vals_slice, keys_pos, keys_neg, keys_up,
                                               ("kn", keys_neg), ("ku", keys_up), ("vu", vals_up))}
     out_host = torch.empty(keys_pos.numel(), dtype=torch.int64).pin_memory()
     stream = torch.cuda.current_stream(dev)
+    for _, t in tables:
+        t.set_host_direct(args.host_direct)
 
     def step():
         for name, t in tables:
@@ -493,7 +498,9 @@ def bench_e2e(args, tables, keys_slice, vals_slice, keys_pos, keys_neg, keys_up,
                  + keys_slice.numel() * 8)
     d2h = n_t * (keys_pos.numel() * 8 + keys_neg.numel() * 8)
     return {"value": round(e2e_value, 4), "unit": UNIT,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "host_buffers": ["staged through device chunks", "inputs read in place, results staged",
+                             "read and written in place"][args.host_direct]}
 
 
 # ---------------------------------------------------------------------------

@@ -167,7 +167,20 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  probe sequence the lane path follows, one per wave, before an op still
  *  open goes to the tiles.  Default: the whole sequence when streaming, 4 in
  *  32-op chunks. */
-enum { WS_OPT_PRELOAD = 1, WS_OPT_PHASED = 2, WS_OPT_LANE_WAVES = 3, WS_OPT_STREAM = 4 };
+/*  WS_OPT_HOST_DIRECT (0..2, default 1): what a call does with host
+ *  buffers that are page-locked and mapped into the device's address space
+ *  (cudaHostAlloc / cudaMallocHost / cudaHostRegister memory with unified
+ *  addressing).  0: every host buffer is staged through the table's device
+ *  chunks (copy engines, double-buffered against the kernels).  1: the
+ *  kernels read keys, values and op codes in place over the host link; host
+ *  result buffers are still staged.  2: results are written in place too.
+ *  Pageable host memory is always staged.  The caller must not touch the
+ *  buffers until the call's work on its stream has completed.  Measured on
+ *  a GB300 with its Grace host (2^28-slot tables, the four designs' insert /
+ *  query / upsert / erase step with pinned buffers): 7.9 Gops/s staged, 9.2
+ *  with inputs in place, 6.8 with results written in place as well (scattered
+ *  small writes over the host link cost more than one bulk copy). */
+enum { WS_OPT_PRELOAD = 1, WS_OPT_PHASED = 2, WS_OPT_LANE_WAVES = 3, WS_OPT_STREAM = 4, WS_OPT_HOST_DIRECT = 5 };
 ws_status ws_set_option(ws_table* t, int option, int64_t value);
 
 /* Insert-if-unique (§5.1 Upsert with the empty callback).  status_out: per-op

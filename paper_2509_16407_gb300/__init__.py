@@ -160,6 +160,10 @@ class Table:
         """Streaming lanes in single-table calls (on by default) or 32-op chunks."""
         _check(lib().ws_set_option(self._h, 4, int(bool(on))), "ws_set_option")
 
+    def set_host_direct(self, mode: int):
+        """Page-locked host buffers: 0 staged, 1 inputs read in place, 2 results written in place too."""
+        _check(lib().ws_set_option(self._h, 5, int(mode)), "ws_set_option")
+
     def clear(self, stream=None):
         _check(lib().ws_clear(self._h, self._stream(stream)), "ws_clear")
 

@@ -110,9 +110,31 @@ int wsi::classify(const void* p, int device) {
   return PTR_HOST;
 }
 
+void* wsi::mapped_host(const void* p) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 namespace {
 
 bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
+
+// WS_OPT_HOST_DIRECT: replace a host pointer by the device's view of it when
+// the memory is page-locked and mapped, so the kernel reads (and writes) it
+// in place over the host link instead of through the staging copies.
+template <typename P>
+void go_direct(P& p, int& cls) {
+  if (cls != wsi::PTR_HOST) return;
+  void* d = wsi::mapped_host(p);
+  if (!d) return;
+  p = reinterpret_cast<P>(d);
+  cls = wsi::PTR_DEVICE;
+}
 
 }  // namespace
 
@@ -141,8 +163,8 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
   if (kind == ws::KIND_MIXED && !ops) return WS_ERR_INVALID;
   DeviceGuard guard(t->device);
 
-  const int pk = classify(keys, t->device), pv = classify(vals, t->device), po = classify(ops, t->device);
-  const int pvo = classify(vals_out, t->device), pst = classify(status_out, t->device);
+  int pk = classify(keys, t->device), pv = classify(vals, t->device), po = classify(ops, t->device);
+  int pvo = classify(vals_out, t->device), pst = classify(status_out, t->device);
   if (pk == PTR_OTHER_DEVICE || pv == PTR_OTHER_DEVICE || po == PTR_OTHER_DEVICE ||
       pvo == PTR_OTHER_DEVICE || pst == PTR_OTHER_DEVICE)
     return WS_ERR_INVALID;
@@ -154,6 +176,15 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
   tv.shortcut = t->never_erased;
   t->last_stream = s;
 
+  if (t->host_direct >= 1) {  // inputs read in place
+    go_direct(keys, pk);
+    go_direct(vals, pv);
+    go_direct(ops, po);
+  }
+  if (t->host_direct >= 2) {  // results written in place
+    go_direct(vals_out, pvo);
+    go_direct(status_out, pst);
+  }
   const bool any_host = pk == PTR_HOST || pv == PTR_HOST || po == PTR_HOST || pvo == PTR_HOST || pst == PTR_HOST;
   if (!any_host) {
     ws::BatchArgs a{keys, vals, ops, vals_out, status_out, n, op, 1, 0};
@@ -435,6 +466,10 @@ ws_status ws_set_option(ws_table* t, int option, int64_t value) {
     case WS_OPT_STREAM:
       if (value != 0 && value != 1) return WS_ERR_INVALID;
       t->tv.stream = (int)value;
+      return WS_OK;
+    case WS_OPT_HOST_DIRECT:
+      if (value < 0 || value > 2) return WS_ERR_INVALID;
+      t->host_direct = (int)value;
       return WS_OK;
   }
   return WS_ERR_INVALID;

@@ -61,6 +61,7 @@ struct ws_table {
   int T = 0, scheme = 0, meta = 0, device = 0, num_sms = 0;
   uint32_t pmax = 0, spin = 0;
   int never_erased = 1;
+  int host_direct = 1;  // WS_OPT_HOST_DIRECT
   wsi::u64 bytes = 0;
   cudaStream_t last_stream = nullptr;
   wsi::Staging* stage = nullptr;
@@ -73,6 +74,9 @@ cudaError_t dispatch(const ws_table* t, const ws::TableView& tv, const ws::Batch
 // 1 device pointer on `device`, 2 host, 3 another device, 0 null.
 int classify(const void* p, int device);
 enum { PTR_NULL = 0, PTR_DEVICE = 1, PTR_HOST = 2, PTR_OTHER_DEVICE = 3 };
+// The device's view of page-locked, mapped host memory, or null (pageable
+// memory, or a pointer that is not host memory).
+void* mapped_host(const void* p);
 // Table constructor; with a non-null stream it allocates and clears on that
 // stream without synchronising the device.
 ws_status table_create(const ws_config* cfg, cudaStream_t stream, ws_table** out);

@@ -459,3 +459,39 @@ def test_rehash_into_larger_table(ws, oracle_mod, scheme, meta):
         check_layout(oracle_mod, dst, om.count())
         assert dst.last_error()["status"] == 0
         dst.close()
+
+
+# --------------------------------------------------------------------------
+# page-locked host buffers read (and written) in place by the kernels
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [1, 2])
+@pytest.mark.parametrize("scheme,meta", DESIGNS, ids=DESIGN_IDS)
+def test_host_direct_matches_oracle(ws, oracle_mod, scheme, meta, mode):
+    import torch
+    t = ws.Table(1 << 18, scheme, meta)
+    t.set_host_direct(mode)
+    S = t.info()["slots"]
+    n = int(0.8 * S)
+    both = W.distinct_keys(909 + mode, n + n // 4)
+    keys, absent = both[:n], both[n:]
+    vals = W.splitmix64(910, n)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).pin_memory()
+    om = oracle_mod.OracleMap()
+    st = t.insert(pin(keys), pin(vals), return_status=True)
+    torch.cuda.synchronize()
+    assert (st.numpy() == om.insert(keys, vals)).all()
+    q = np.concatenate([keys[::2], absent])
+    out = torch.empty(q.size, dtype=torch.int64).pin_memory()
+    _, qs = t.query(pin(q), out=out, return_status=True)
+    torch.cuda.synchronize()
+    want, wst = om.query(q)
+    assert (out.numpy().view(np.uint64) == want).all() and (qs.numpy() == wst).all()
+    ops, mk, mv = W.mixed_batch(911, n_ops=1 << 14, universe=1 << 13)
+    gv, gs = t.mixed(torch.from_numpy(ops).pin_memory(), pin(mk), pin(mv))
+    torch.cuda.synchronize()
+    ov, os_ = om.mixed(ops, mk, mv)
+    qm = ops == W.MX_QUERY
+    assert (host(gv)[qm] == ov[qm]).all() and (host(gs)[qm] == os_[qm]).all()
+    assert t.count() == om.count()
+    check_layout(oracle_mod, t, om.count())
+    t.close()
