@@ -170,6 +170,11 @@ __device__ __forceinline__ void st_slot_relaxed(Slot* p, u64 k, u64 v) {
 __device__ __forceinline__ void st_tag_release(u16* p, u16 v) {
   asm volatile("st.release.gpu.global.b16 [%0], %1;" ::"l"(p), "h"(v) : "memory");
 }
+// The TOMB tag of an erase in a launch where nothing claims slots (an
+// erase-only call): no claimer can observe it before the launch ends.
+__device__ __forceinline__ void st_tag_relaxed(u16* p, u16 v) {
+  asm volatile("st.relaxed.gpu.global.b16 [%0], %1;" ::"l"(p), "h"(v) : "memory");
+}
 
 __device__ __forceinline__ u32 ld_u32_relaxed(const u32* p) {
   u32 v;

@@ -880,6 +880,12 @@ struct TileOps {
     return st;
   }
 
+  // TOMB_RELEASE: publish the TOMB tag with release semantics, so that a
+  // claimer of the freed tag in the same launch finds the pair's CAS ordered
+  // before its own pair store.  An erase-only launch claims nothing (calls on
+  // a table are ordered, and batched phases run their op kinds as separate,
+  // stream-ordered kernels), so there a relaxed store suffices.
+  template <bool TOMB_RELEASE = true>
   __device__ static u8 do_erase(const TableView& tv_in, const TileCtx<T>& c, u64 K, u64 h1, u64 h2, PreRef pre,
                                 u64& out, int& dcount) {
     TableView tv = tv_in;  // through L2, as for do_upsert
@@ -892,7 +898,12 @@ struct TileOps {
       int ok = 0;
       if (c.tl == 0) {
         ok = ptx::cas_slot(tv.slots + h.idx, K, h.val, KEY_TOMB, 0) ? 1 : 0;
-        if (ok && META) ptx::st_tag_release(tv.tags + h.idx, TAG_TOMB);
+        if (ok && META) {
+          if (TOMB_RELEASE)
+            ptx::st_tag_release(tv.tags + h.idx, TAG_TOMB);
+          else
+            ptx::st_tag_relaxed(tv.tags + h.idx, TAG_TOMB);
+        }
       }
       if (c.shfl(ok, 0)) {
         out = h.val;
@@ -1116,7 +1127,7 @@ struct TileOps {
 
   __device__ static __forceinline__ int lane_wave(const TableView& tv, PreRef p, u64 K, u64 V, int op, int opk,
                                                   u32 w, u64 bw, LaneState& ls, u64& out, u8& st, int& dcount,
-                                                  bool& fresh) {
+                                                  bool& fresh, bool tomb_release) {
     Snap sn = snap_of(p, K, ls.tsum);
     if (sn.unsure) return -1;
     if (sn.hit >= 0) {
@@ -1136,7 +1147,12 @@ struct TileOps {
         fresh = false;
         return -1;
       }
-      if (META) ptx::st_tag_release(tv.tags + idx, TAG_TOMB);
+      if (META) {  // see do_erase
+        if (tomb_release)
+          ptx::st_tag_release(tv.tags + idx, TAG_TOMB);
+        else
+          ptx::st_tag_relaxed(tv.tags + idx, TAG_TOMB);
+      }
       out = v;
       --dcount;
       st = ST_FOUND;
@@ -1531,7 +1547,8 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
       if (want) {
         snap_wave = (int)w;
         const PreRef p{&sm.pre, lane};
-        const int r = Ops::lane_wave(tv, p, K, V, op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh);
+        const int r =
+            Ops::lane_wave(tv, p, K, V, op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh, KIND != KIND_ERASE);
         if (r > 0) {
           done = true;
         } else if (r == -2 && kLaneLock && pass == 0 && !locked) {
@@ -1581,7 +1598,7 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
         sj = lockfree ? Ops::template do_upsert<true>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, pre, tile_d)
                       : Ops::template do_upsert<false>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, pre, tile_d);
       } else if (KIND == KIND_ERASE) {
-        sj = Ops::do_erase(tv, c, Kj, h1j, h2j, pre, o, tile_d);
+        sj = Ops::template do_erase<false>(tv, c, Kj, h1j, h2j, pre, o, tile_d);  // an erase-only launch
       } else {
         sj = Ops::do_mixed(tv, c, sm.op[j], Kj, h1j, h2j, sm.val[j], pre, o, tile_d);
       }
@@ -1739,7 +1756,8 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           r = Ops::lane_wave_lines(tv, p, sm.key[lane], sm.val[lane], op, opk, w, sm.bw[lane], ls, out, st, dcount,
                                    fresh);
         else
-          r = Ops::lane_wave(tv, p, sm.key[lane], sm.val[lane], op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh);
+          r = Ops::lane_wave(tv, p, sm.key[lane], sm.val[lane], op, opk, w, sm.bw[lane], ls, out, st, dcount, fresh,
+                             KIND != KIND_ERASE);
         const bool wrote = r > 0 && st == ST_INSERTED;
         if (r > 0) {
           const u64 gi = sm.out[lane];
@@ -1795,7 +1813,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           sj = lockfree ? Ops::template do_upsert<true>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, no_pre(), rd)
                         : Ops::template do_upsert<false>(tv, c, Kj, h1j, h2j, sm.val[j], upsert_op, no_pre(), rd);
         } else if (KIND == KIND_ERASE) {
-          sj = Ops::do_erase(tv, c, Kj, h1j, h2j, no_pre(), o, rd);
+          sj = Ops::template do_erase<false>(tv, c, Kj, h1j, h2j, no_pre(), o, rd);  // an erase-only launch
         } else {
           sj = Ops::do_mixed(tv, c, sm.op[j], Kj, h1j, h2j, sm.val[j], no_pre(), o, rd);
         }
