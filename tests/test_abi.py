@@ -56,4 +56,5 @@ def test_host_side_checks_without_gpu(L):
     assert L.ws_insert(None, None, None, 0, None) == 1
     assert L.ws_count(None, None) == 1
     assert L.ws_destroy(None) == 1
+    assert L.ws_set_option(None, 5, 1) == 1  # WS_OPT_HOST_DIRECT on a null table
     assert L.ws_status_string(4) == b"an insert found no free slot"
