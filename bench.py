@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--sweep", default="", help="write the load/tile sweep as JSON lines to this file")
     p.add_argument("--sweep-log2-slots", default="28,22")
     p.add_argument("--aging-log2-slots", type=int, default=26)
-    p.add_argument("--aging-iters", type=int, default=300)
+    p.add_argument("--aging-iters", type=int, default=1000)
     p.add_argument("--workload", default="config2", choices=["config2", "batched", "serve", "aging", "phased", "mixed"],
                    help="config2 = the default line; batched = 1024 uneven tables in one graph launch")
     p.add_argument("--tables", type=int, default=1024)
@@ -842,7 +842,7 @@ def bench_aging(args):
             era = pool[it * m: (it + 1) * m]
             pos = pool[(it + 1) * m: (it + 2) * m]
             neg = negp[it * m: (it + 1) * m]
-            if it in (0, iters // 2, iters - 1):
+            if it % max(1, iters // 20) == 0 or it == iters - 1:
                 costs = {}
                 for ph, k in (("insert", ins), ("positive", pos), ("negative", neg), ("delete", era)):
                     c, _ = t.probe_cost(k[: 1 << 16])
@@ -860,10 +860,13 @@ def bench_aging(args):
         ms = np.array([a.elapsed_time(b) for a, b in times])
         cnt = t.count()
         err = t.last_error()
+        mean_probes = {ph: round(float(np.mean([c[ph] for c in probes.values()])), 3)
+                       for ph in ("insert", "positive", "negative", "delete")}
         out[name] = {"gops_mean": round(4 * m / ms.mean() / 1e6, 3), "gops_first10": round(4 * m / ms[:10].mean() / 1e6, 3),
                      "gops_last10": round(4 * m / ms[-10:].mean() / 1e6, 3), "iter_ms_p50": round(float(np.median(ms)), 4),
                      "iter_ms_p99": round(float(np.percentile(ms, 99)), 4), "count_after": cnt, "count_expected": fill,
                      "failed_ops": err, "probe_lines": probes,
+                     "probe_lines_mean_over_samples": mean_probes,
                      "paper_table1_aging_probes(ins,pos,neg,del)": TABLE1_AGING[name]}
         t.close()
         torch.cuda.empty_cache()
