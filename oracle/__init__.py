@@ -10,8 +10,9 @@ phase semantics; see ``ws_oracle.cpp`` for the rules.  Its layout checker
 re-derives legal placements from the written hash/probe specification.
 
 Parity status: the map semantics are pinned (brute force, closed forms and
-invariants in ``tests/test_oracle_pins.py``); the layout checker is pinned by
-planted-mistake layouts in the same file.
+invariants in ``tests/test_oracle_pins.py``); the layout checker and the
+probe-count recount are pinned by planted layouts with hand-counted results in
+the same file.
 """
 from __future__ import annotations
 
@@ -76,6 +77,8 @@ def lib():
         L.ora_candidates_full.argtypes = [vp, vp, u64, u64, i32, u64, u64, u64, vp, u64, vp]
         L.ora_primary_bucket.argtypes = [vp, u64, u64, u64, vp]
         L.ora_iceberg_buckets.argtypes = [vp, u64, u64, u64, u64, vp]
+        L.ora_probe_cost.argtypes = [vp, vp, u64, u64, i32, u64, u64, u64, u64, i32, vp, u64, vp, vp]
+        L.ora_probe_cost.restype = i32
         _lib = L
     return _lib
 
@@ -171,6 +174,22 @@ def candidates_full(slots, tags, nb, B, scheme, pmax, seed1, seed2, keys):
     lib().ora_candidates_full(_p(s), _p(t), nb, B, scheme, pmax, seed1, seed2,
                               _p(k), k.size, _p(out))
     return out.astype(bool)
+
+
+def probe_cost(slots, tags, nb, B, scheme, pmax, seed1, seed2, tile, never_erased, keys):
+    """Host recount of the probe count (cache lines, 32-byte sectors) a query
+    of each key pays on a dumped table, and whether the key is present.
+    Returns (lines u64[n], sectors u64[n], found bool[n])."""
+    s = _u64(slots)
+    t = None if tags is None else np.ascontiguousarray(tags, dtype=np.uint16)
+    k = _u64(keys)
+    cost = np.empty(k.size, np.uint64)
+    found = np.empty(k.size, np.uint8)
+    rc = lib().ora_probe_cost(_p(s), _p(t), nb, B, scheme, pmax, seed1, seed2, tile, int(bool(never_erased)),
+                              _p(k), k.size, _p(cost), _p(found))
+    if rc != 0:
+        raise ValueError("probe_cost: bad geometry")
+    return cost >> np.uint64(32), cost & np.uint64(0xFFFFFFFF), found.astype(bool)
 
 
 def primary_bucket(keys, nb, seed1):

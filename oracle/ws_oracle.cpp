@@ -386,6 +386,123 @@ void ora_candidates_full(const uint64_t* slots, const uint16_t* tags, uint64_t n
   }
 }
 
+// Probe count (§5 "probe count", Table 1) recounted on a dumped table: the
+// memory a query of each key touches, per the cost model the library
+// documents for ws_probe_cost.  The query reads buckets along the key's
+// candidate sequence in tile steps of `tile` consecutive 16-byte slots:
+//   * plain buckets: a tile of T <= B lanes reads a bucket in B/T steps of T
+//     slots (T/2 sectors, ceil(16T/128) lines each); a tile of T > B lanes
+//     reads T/B buckets of the sequence side by side in one step (B/2
+//     sectors and one line per bucket in range).  The scan of a key stops at
+//     the step holding the key, and after a step in which some slot is EMPTY
+//     it leaves the bucket (EMPTY slots form a suffix: nothing follows them);
+//   * double hashing (§2.2) stops there for good -- an EMPTY slot means the
+//     key was never placed further on -- and otherwise visits at most pmax
+//     buckets (clamped to nb);
+//   * two choice (§2.2) reads b_0, then b_1, except that a table that has
+//     never seen an erase skips b_1 once b_0 holds fewer than 3B/4 live keys
+//     (the placement shortcut makes b_1 unused then);
+//   * fingerprint buckets (§4.3): the 64-byte tag line of the bucket (2
+//     sectors, 1 line), then each slot whose tag equals tag(k), in slot order,
+//     until the key (1 sector and 1 line each).  Double hashing stops after a
+//     bucket with an EMPTY tag; iceberg after a front bucket with an EMPTY
+//     tag; two choice as above with the occupancy counted on the tags.
+// cost_out[i] = (lines << 32) | sectors; found_out[i] = 1 when k is present.
+// Sentinel keys get cost 0 and found 0.  Returns -1 on a bad geometry.
+int ora_probe_cost(const uint64_t* slots, const uint16_t* tags, uint64_t nb, uint64_t B, int scheme,
+                   uint64_t pmax, uint64_t seed1, uint64_t seed2, uint64_t tile, int never_erased,
+                   const uint64_t* keys, uint64_t n, uint64_t* cost_out, uint8_t* found_out) {
+  if (nb == 0 || (nb & (nb - 1)) != 0 || B == 0 || tile == 0) return -1;
+  if (tags && B != 32) return -1;
+  const uint64_t mask = nb - 1;
+  const uint64_t fill_shortcut = 3 * B / 4;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t k = keys[i];
+    cost_out[i] = 0;
+    if (found_out) found_out[i] = 0;
+    if (is_sentinel(k)) continue;
+    const uint64_t h1 = fmix(k ^ seed1), h2 = fmix(k ^ seed2);
+    // the candidate buckets, in probe order
+    std::vector<uint64_t> seq;
+    if (scheme == 0) {
+      const uint64_t P = pmax < nb ? pmax : nb;
+      for (uint64_t j = 0; j < P; ++j) seq.push_back((h1 + j * (h2 | 1ull)) & mask);
+    } else if (scheme == 2) {
+      const IcebergBuckets ib = iceberg_buckets(nb, h1, h2);
+      seq = {ib.front, ib.back1, ib.back2};
+    } else {
+      const uint64_t b0 = h1 & mask;
+      seq.push_back(b0);
+      if (nb > 1) {
+        uint64_t b1 = h2 & mask;
+        if (b1 == b0) b1 = (b0 + 1) & mask;
+        seq.push_back(b1);
+      }
+    }
+    uint64_t lines = 0, sectors = 0;
+    bool found = false;
+    if (tags) {
+      const uint16_t kt = spec_tag(k);
+      for (size_t j = 0; j < seq.size() && !found; ++j) {
+        const uint64_t b = seq[j];
+        sectors += 2;
+        lines += 1;
+        bool has_empty = false;
+        uint64_t live = 0;
+        for (uint64_t q = 0; q < 32; ++q) {
+          const uint16_t t = tags[b * 32 + q];
+          if (t == 0) has_empty = true;
+          if (t >= 2) ++live;
+        }
+        for (uint64_t q = 0; q < 32 && !found; ++q) {
+          if (tags[b * 32 + q] != kt) continue;
+          sectors += 1;
+          lines += 1;
+          if (slots[2 * (b * 32 + q)] == k) found = true;
+        }
+        if (found) break;
+        if (scheme == 0 && has_empty) break;
+        if (scheme == 2 && j == 0 && has_empty) break;
+        if (scheme == 1 && j == 0 && never_erased && live < fill_shortcut) break;
+      }
+    } else {
+      const uint64_t G = tile > B ? tile / B : 1;          // buckets per step
+      const uint64_t W = tile > B ? B : tile;              // slots of a bucket per step
+      const uint64_t step_lines = (W * 16 + 127) / 128;
+      for (size_t j = 0; j < seq.size() && !found; j += G) {
+        const uint64_t nact = std::min<uint64_t>(G, seq.size() - j);
+        bool ended = false;
+        uint64_t live0 = 0;
+        for (uint64_t s = 0; s * W < B; ++s) {
+          sectors += nact * (W / 2);
+          lines += nact * step_lines;
+          bool empty_here = false;
+          for (uint64_t g = 0; g < nact; ++g) {
+            const uint64_t b = seq[j + g];
+            for (uint64_t q = s * W; q < (s + 1) * W; ++q) {
+              const uint64_t kq = slots[2 * (b * B + q)];
+              if (kq == k) found = true;
+              if (kq == K_EMPTY) empty_here = true;
+              if (kq != K_EMPTY && kq != K_TOMB) ++live0;
+            }
+          }
+          if (found) break;
+          if (empty_here) {
+            ended = true;
+            break;
+          }
+        }
+        if (found) break;
+        if (scheme == 0 && ended) break;
+        if (scheme == 1 && G == 1 && j == 0 && never_erased && live0 < fill_shortcut) break;
+      }
+    }
+    cost_out[i] = (lines << 32) | sectors;
+    if (found_out) found_out[i] = found ? 1 : 0;
+  }
+  return 0;
+}
+
 // Primary bucket (b_0) under the specification; the adversarial benchmark of
 // §4.1 needs it on the host to build keys with a chosen primary bucket.
 void ora_primary_bucket(const uint64_t* keys, uint64_t n, uint64_t nb, uint64_t seed1,

@@ -441,6 +441,158 @@ def test_layout_checker_iceberg_planted(oracle_mod):
     assert full() == [False]
 
 
+# --------------------------------------------------------------------------
+# probe-count recount (§5 "probe count", Table 1): hand-counted planted
+# layouts.  Plain buckets cost T/2 sectors and one 128-byte line per step of
+# a T-lane tile (T/B buckets side by side when T > B); fingerprint buckets
+# cost a 64-byte tag line (2 sectors, 1 line) plus one sector and one line per
+# candidate slot read.
+# --------------------------------------------------------------------------
+def _filler(rng, avoid, low16=None):
+    while True:
+        f = rng.getrandbits(64)
+        if low16 is not None:
+            f = (f & ~0xFFFF) | low16
+        if f not in SENT and f not in avoid and (f & 0xFFFF) >= 2:
+            return f
+
+
+def test_probe_cost_planted_double_plain(oracle_mod):
+    nb, B = 16, 8
+    S = nb * B
+    k, seq = _key_with_distinct_seq(nb, 3)
+    rng = random.Random(5)
+
+    def fresh():
+        return np.zeros(2 * S, np.uint64)
+
+    def fill(s, b, upto=B, skip=()):
+        for j in range(upto):
+            if j not in skip:
+                s[2 * (b * B + j)] = _filler(rng, {k})
+
+    def cost(s, tile, pmax=80, key=k):
+        lines, sec, found = oracle_mod.probe_cost(s, None, nb, B, 0, pmax, S1, S2, tile, 1,
+                                                  np.array([key], np.uint64))
+        return int(lines[0]), int(sec[0]), bool(found[0])
+
+    s = fresh()
+    assert cost(s, 8) == (1, 4, False)          # b_0 empty: one line, then stop
+    s[2 * (seq[0] * B + 3)] = k
+    fill(s, seq[0], 3)
+    assert cost(s, 8) == (1, 4, True)           # found in b_0
+    assert cost(s, 4) == (1, 2, True)           # tile 4: slot 3 is in the first step
+    s = fresh(); fill(s, seq[0], 5); s[2 * (seq[0] * B + 5)] = k
+    assert cost(s, 4) == (2, 4, True)           # slot 5: second step of a 4-lane tile
+    assert cost(s, 16) == (2, 8, True)          # 16 lanes read b_0 and b_1 side by side
+    s = fresh(); fill(s, seq[0]); s[2 * (seq[1] * B)] = k
+    assert cost(s, 8) == (2, 8, True)           # b_0 full, key in b_1
+    assert cost(s, 16) == (2, 8, True)
+    s = fresh(); fill(s, seq[0])
+    assert cost(s, 8) == (2, 8, False)          # b_0 full, b_1 empty: a miss after two lines
+    s = fresh(); fill(s, seq[0]); fill(s, seq[1]); s[2 * (seq[2] * B + 7)] = k; fill(s, seq[2], 7)
+    assert cost(s, 8) == (3, 12, True)
+    assert cost(s, 16) == (4, 16, True)         # second step of two buckets
+    assert cost(s, 4) == (6, 12, True)          # two steps per bucket, key in the last one
+    # tombstones do not end a scan
+    s = fresh()
+    for j in range(B):
+        s[2 * (seq[0] * B + j)] = (1 << 64) - 1
+    s[2 * (seq[1] * B)] = k
+    assert cost(s, 8) == (2, 8, True)
+    # the probe cap: every bucket full, key absent, pmax = 3
+    s = fresh()
+    for b in range(nb):
+        fill(s, b)
+    assert cost(s, 8, pmax=3) == (3, 12, False)
+    assert cost(s, 16, pmax=3) == (3, 12, False)   # steps of 2 + 1 buckets
+    assert cost(s, 8, pmax=80) == (nb, 4 * nb, False)  # clamped to nb
+    assert cost(s, 8, key=0) == (0, 0, False)      # sentinel
+
+
+def test_probe_cost_planted_two_choice_plain(oracle_mod):
+    nb, B = 16, 32
+    S = nb * B
+    rng = random.Random(9)
+    while True:
+        k = rng.getrandbits(64)
+        b0, b1 = _fmix(k ^ S1) % nb, _fmix(k ^ S2) % nb
+        if b0 != b1:
+            break
+
+    def fresh():
+        return np.zeros(2 * S, np.uint64)
+
+    def fill(s, b, upto):
+        for j in range(upto):
+            s[2 * (b * B + j)] = _filler(rng, {k})
+
+    def cost(s, never_erased, tile=8):
+        lines, sec, found = oracle_mod.probe_cost(s, None, nb, B, 1, 2, S1, S2, tile, never_erased,
+                                                  np.array([k], np.uint64))
+        return int(lines[0]), int(sec[0]), bool(found[0])
+
+    s = fresh(); fill(s, b0, 12)
+    assert cost(s, 1) == (2, 8, False)      # 12 live < 24: the never-erased shortcut skips b_1
+    assert cost(s, 0) == (3, 12, False)     # with erases behind it, b_1 is read too
+    s = fresh(); fill(s, b0, 28)
+    assert cost(s, 1) == (5, 20, False)     # 28 live: b_0 in four lines, then b_1's first
+    s = fresh(); fill(s, b0, 32); fill(s, b1, 20); s[2 * (b1 * B + 20)] = k
+    assert cost(s, 1) == (7, 28, True)      # b_0 whole, b_1 up to slot 20 (third line)
+    assert cost(s, 1, tile=32) == (8, 32, True)   # a 32-lane tile reads a bucket (four lines) per step
+
+
+def test_probe_cost_planted_metadata(oracle_mod):
+    nb, B = 16, 32
+    S = nb * B
+    rng = random.Random(13)
+    k, seq = _key_with_distinct_seq(nb, 21)
+
+    def fresh():
+        return np.zeros(2 * S, np.uint64), np.zeros(S, np.uint16)
+
+    def put(s, t, b, j, key):
+        s[2 * (b * B + j)] = key
+        t[b * B + j] = _tag(key)
+
+    def fill(s, t, b, upto, collide=()):
+        for j in range(upto):
+            f = _filler(rng, {k}, low16=(k & 0xFFFF) if j in collide else None)
+            if j not in collide:
+                while _tag(f) == _tag(k):
+                    f = _filler(rng, {k})
+            put(s, t, b, j, f)
+
+    def cost(s, t, scheme, never_erased=1, P=80):
+        lines, sec, found = oracle_mod.probe_cost(s, t, nb, B, scheme, P, S1, S2, 4, never_erased,
+                                                  np.array([k], np.uint64))
+        return int(lines[0]), int(sec[0]), bool(found[0])
+
+    # double hashing: a tag collision in slot 2, the key in slot 5 of b_0
+    s, t = fresh(); fill(s, t, seq[0], 5, collide=(2,)); put(s, t, seq[0], 5, k)
+    assert cost(s, t, 0) == (3, 4, True)    # tag line + two candidates
+    s, t = fresh(); fill(s, t, seq[0], 32)
+    assert cost(s, t, 0) == (2, 4, False)   # full b_0 without a match, empty b_1: two tag lines
+    s, t = fresh(); fill(s, t, seq[0], 32, collide=(7, 30))
+    assert cost(s, t, 0) == (4, 6, False)   # two candidates read in vain
+    # two choice: the shortcut on the tags' occupancy
+    b0 = _fmix(k ^ S1) % nb
+    s, t = fresh(); fill(s, t, b0, 10)
+    assert cost(s, t, 1, 1, 2) == (1, 2, False)
+    assert cost(s, t, 1, 0, 2) == (2, 4, False)
+    s, t = fresh(); fill(s, t, b0, 24)
+    assert cost(s, t, 1, 1, 2) == (2, 4, False)   # 24 live: not below 3/4, b_1 read
+    # iceberg: a front bucket with an EMPTY slot ends the scan
+    front = int(oracle_mod.iceberg_buckets(np.array([k], np.uint64), nb, S1, S2)[0, 0])
+    s, t = fresh(); fill(s, t, front, 31)
+    assert cost(s, t, 2) == (1, 2, False)
+    s, t = fresh(); fill(s, t, front, 32)
+    assert cost(s, t, 2) == (3, 6, False)         # full front: both backyard buckets
+    t[front * B + 31] = 1                          # a tombstone is not EMPTY: still all three
+    s[2 * (front * B + 31)] = (1 << 64) - 1
+    assert cost(s, t, 2) == (3, 6, False)
+
+
 def test_primary_bucket_is_h1(oracle_mod):
     keys = W.distinct_keys(3, 64)
     pb = oracle_mod.primary_bucket(keys, 1 << 10, S1)
