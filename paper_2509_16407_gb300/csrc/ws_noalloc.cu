@@ -18,6 +18,7 @@
 // each call rewrites the descriptors it uses and zeroes its work tickets.
 // Calls whose work overlaps on the GPU race on the array -- order them on one
 // stream or synchronise between them.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -66,8 +67,14 @@ int kind_of(int bk) {
 }
 
 // Host-side staging of one call's descriptors (per thread, no heap).
+constexpr uint32_t kTableSlots = 2 * kMaxItems;  // open-addressing set of the call's tables
 struct HostStage {
   uint32_t order[kMaxItems];
+  int64_t key[kMaxItems];          // sort key of each item (phase, menu entry, kind)
+  uint32_t phase_idx[kMaxItems];   // index of the item's phase among the call's phases
+  uint32_t table_slot[kMaxItems];  // slot of the item's table in `tables`
+  ws_table* tables[kTableSlots];
+  uint32_t erased_phases[kTableSlots];  // bit p: the table is erased in phase p of the call
   ws::MultiItem items[kMaxItems];
   u32 prefix[kMaxItems + 1];
   u32 phase_begin[kMaxPhases + 1];
@@ -114,26 +121,19 @@ extern "C" ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n
   WS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
 
   HostStage& hs = t_stage;
-  // stable order by (phase, menu entry, kind) -- insertion sort: at most
-  // kMaxItems, no allocation; the items of one (entry, kind) run of a phase
-  // form one persistent launch
-  auto sort_key = [&](uint32_t i) {
+  // order by (phase, menu entry, kind), ties by position: the items of one
+  // (entry, kind) run of a phase form one persistent launch.  Keys are
+  // computed once; the sort works in place (no allocation).
+  for (uint32_t i = 0; i < (uint32_t)n_items; ++i) {
     const ws_table* t = items[i].table;
     const int cfg = ws::multi_menu_index(t->scheme, t->meta != 0, (int)t->B, t->T);
-    return ((int64_t)items[i].phase * 16 + (cfg + 1)) * 8 + kind_of(items[i].kind);
-  };
-  for (uint32_t i = 0; i < (uint32_t)n_items; ++i) {
-    uint32_t k = i;
-    const int64_t ki = sort_key(i);
-    while (k > 0 && sort_key(hs.order[k - 1]) > ki) {
-      hs.order[k] = hs.order[k - 1];
-      --k;
-    }
-    hs.order[k] = i;
+    hs.key[i] = ((int64_t)items[i].phase * 16 + (cfg + 1)) * 8 + kind_of(items[i].kind);
+    hs.order[i] = i;
   }
-  // phases; tables erased anywhere in the call lose the two-choice shortcut
-  // for the whole call, and a table erased in a phase takes the locked
-  // insert path in that phase
+  std::sort(hs.order, hs.order + n_items, [&](uint32_t a, uint32_t b) {
+    return hs.key[a] != hs.key[b] ? hs.key[a] < hs.key[b] : a < b;
+  });
+  // phases
   uint32_t n_ph = 0;
   for (uint32_t k = 0; k < (uint32_t)n_items; ++k) {
     const int ph = items[hs.order[k]].phase;
@@ -148,19 +148,31 @@ extern "C" ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n
       hs.phase_begin[n_ph] = k;
       ++n_ph;
     }
+    hs.phase_idx[k] = n_ph - 1;
   }
   hs.phase_begin[n_ph] = (uint32_t)n_items;
+  // tables erased anywhere in the call lose the two-choice shortcut for the
+  // whole call, and a table erased in a phase takes the locked insert path
+  // in that phase: one pass collects, per table, the phases that erase it
+  std::memset(hs.tables, 0, sizeof(hs.tables));
+  for (uint32_t k = 0; k < (uint32_t)n_items; ++k) {
+    ws_table* t = items[hs.order[k]].table;
+    uint32_t h = (uint32_t)((reinterpret_cast<uintptr_t>(t) >> 4) * 0x9E3779B1u) & (kTableSlots - 1);
+    while (hs.tables[h] && hs.tables[h] != t) h = (h + 1) & (kTableSlots - 1);
+    if (!hs.tables[h]) {
+      hs.tables[h] = t;
+      hs.erased_phases[h] = 0;
+    }
+    hs.table_slot[k] = h;
+    if (items[hs.order[k]].kind == WS_BK_ERASE) hs.erased_phases[h] |= 1u << hs.phase_idx[k];
+  }
   hs.prefix[0] = 0;
   uint64_t chunks = 0;
   for (uint32_t k = 0; k < (uint32_t)n_items; ++k) {
     const ws_batch_item& s = items[hs.order[k]];
     const ws_table* t = s.table;
-    bool erased_call = false, erased_phase = false;
-    for (uint64_t q = 0; q < n_items; ++q) {
-      if (items[q].table != t || items[q].kind != WS_BK_ERASE) continue;
-      erased_call = true;
-      if (items[q].phase == s.phase) erased_phase = true;
-    }
+    const uint32_t er = hs.erased_phases[hs.table_slot[k]];
+    const bool erased_call = er != 0, erased_phase = ((er >> hs.phase_idx[k]) & 1u) != 0;
     ws::MultiItem& m = hs.items[k];
     std::memset(&m, 0, sizeof(m));
     m.tv = t->tv;
@@ -181,6 +193,12 @@ extern "C" ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n
     if (chunks > 0xffffffffull) return WS_ERR_INVALID;
     hs.prefix[k + 1] = (u32)chunks;
   }
+  // The call is valid from here on.  Tables it erases lose the shortcut
+  // before anything is enqueued, so an error return below cannot leave a
+  // table with tombstones that later calls would still read with the
+  // shortcut.
+  for (uint64_t i = 0; i < n_items; ++i)
+    if (items[i].kind == WS_BK_ERASE) items[i].table->never_erased = 0;
   cudaStream_t st = (cudaStream_t)stream;
   WS_CUDA(cudaMemcpyAsync(scratch->prefix, hs.prefix, (n_items + 1) * sizeof(u32), cudaMemcpyHostToDevice, st));
   WS_CUDA(cudaMemcpyAsync(scratch->items, hs.items, n_items * sizeof(ws::MultiItem), cudaMemcpyHostToDevice, st));
@@ -204,9 +222,6 @@ extern "C" ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n
       WS_CUDA(dispatch(items[hs.order[k]].table, m.tv, m.a, m.kind, st));
     }
   }
-  for (uint64_t i = 0; i < n_items; ++i) {
-    items[i].table->last_stream = st;
-    if (items[i].kind == WS_BK_ERASE) items[i].table->never_erased = 0;
-  }
+  for (uint64_t i = 0; i < n_items; ++i) items[i].table->last_stream = st;
   return WS_OK;
 }

@@ -3,7 +3,8 @@ memory (a framework's caching allocator holds it all, memory reserved up
 front, or a loop that cannot take cudaFree's device-wide synchronisation).
 Its results must equal those of the allocating entry point (ws_batch_plan_*)
 on the same items, bit for bit, on two calls in a row that reuse the
-library's fixed scratch array.  This file is collected last on purpose."""
+library's fixed scratch array, and the oracle's.  This file is collected last
+on purpose."""
 import ctypes
 
 import numpy as np
@@ -79,7 +80,27 @@ def _realise(specs_in):
     return out
 
 
-def test_noalloc_matches_plan_on_two_calls(ws):
+def _oracle_check(oracle_mod, oms, specs):
+    """Apply each table's items phase by phase to its oracle map and compare
+    the no-alloc call's outputs (the items' keys are distinct per item)."""
+    for (ti, kind, k, v, vo, so, ph, op) in sorted(specs, key=lambda x: (x[6], x[0])):
+        om = oms[ti]
+        keys = host(k)
+        if kind == 0:
+            wst, wv = om.insert(keys, host(v)), None
+        elif kind == 1:
+            wst, wv = om.upsert(keys, host(v), op), None
+        elif kind == 2:
+            wv, wst = om.query(keys)
+        else:
+            wv, wst = om.erase(keys)
+        if so is not None:
+            assert (host(so) == wst).all(), (ti, kind, ph)
+        if vo is not None:
+            assert (host(vo) == wv).all(), (ti, kind, ph)
+
+
+def test_noalloc_matches_plan_on_two_calls(ws, oracle_mod):
     import torch
     L = ws.lib()
     n_tab = len(CONFIGS) * 2
@@ -88,6 +109,7 @@ def test_noalloc_matches_plan_on_two_calls(ws):
     B = [ws.Table(1 << 12, *CONFIGS[i % len(CONFIGS)][:2], bucket_slots=CONFIGS[i % len(CONFIGS)][2],
                   tile=CONFIGS[i % len(CONFIGS)][3]) for i in range(n_tab)]
     stream = torch.cuda.current_stream().cuda_stream
+    oms = [oracle_mod.OracleMap() for _ in range(n_tab)]
     for round_no in range(2):  # two calls in a row, different item layouts
         specs_in, keep = _make_specs(ws, round_no, n_tab)
         sa, sb = _realise(specs_in), _realise(specs_in)
@@ -103,9 +125,31 @@ def test_noalloc_matches_plan_on_two_calls(ws):
                     assert torch.equal(ta, tb), (round_no, x[0], x[1])
             if x[5] is not None:
                 assert (host(x[5]) != 255).all()
-        for ta, tb in zip(A, B):
-            assert ta.count() == tb.count()
+        _oracle_check(oracle_mod, oms, sa)
+        for ta, tb, om in zip(A, B, oms):
+            assert ta.count() == tb.count() == om.count()
         assert L.ws_batch_plan_destroy(h) == 0
+
+
+def test_noalloc_takes_no_device_memory(ws):
+    """After a first call (which looks up the scratch array and loads the
+    kernels), further calls leave the device's free memory unchanged."""
+    import torch
+    L = ws.lib()
+    n_tab = len(CONFIGS)
+    A = [ws.Table(1 << 12, *CONFIGS[i][:2], bucket_slots=CONFIGS[i][2], tile=CONFIGS[i][3]) for i in range(n_tab)]
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    specs_in, keep = _make_specs(ws, 0, n_tab)
+    sa = _realise(specs_in)
+    arr = _items(ws, A, sa)
+    assert L.ws_batch_run_noalloc(arr, len(sa), stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert L.ws_batch_run_noalloc(arr, len(sa), stream) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
 
 
 def test_noalloc_rejects_oversized_calls(ws):
@@ -119,3 +163,11 @@ def test_noalloc_rejects_oversized_calls(ws):
         arr[i] = _lib.WsBatchItem(t.handle.value, ws.BK_QUERY, 0, 0, 0, k.data_ptr(), None, k.data_ptr(), None, 4)
     assert L.ws_batch_run_noalloc(arr, 1025, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 1
     assert b"maximum of 1024" in L.ws_cuda_error_string()
+    # 17 distinct phases (empty items are enough): rejected with its reason
+    arr = (_lib.WsBatchItem * 17)()
+    for i in range(17):
+        arr[i] = _lib.WsBatchItem(t.handle.value, ws.BK_QUERY, 0, i, 0, k.data_ptr(), None, k.data_ptr(), None, 0)
+    assert L.ws_batch_run_noalloc(arr, 17, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 1
+    assert b"more than 16 distinct phases" in L.ws_cuda_error_string()
+    # 16 are accepted
+    assert L.ws_batch_run_noalloc(arr, 16, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)) == 0

@@ -208,6 +208,54 @@ def mixed_batch(batch_seed: int, n_ops: int = 1 << 24, universe: int = 1 << 26,
     return ops, keys, vals
 
 
+def mixed_batch_codes(batch_seed: int, n_ops: int = 1 << 20, universe: int = 1 << 18, s: float = 0.99,
+                      universe_seed: int = 0):
+    """A mixed batch that uses every op code: Zipf(s) keys over ``universe``
+    ranks; a key's code is fixed for the batch by a splitmix64 draw of
+    key ^ batch_seed mod 20 (0-3 add, 4-5 max, 6-7 replace, 8-9 insert,
+    10-17 query, 18-19 erase), so every key has one code per batch and the
+    query / erase / upsert classes are key-disjoint.  Draws are taken in
+    order (no quotas: the mix follows the Zipf mass of each class).  Values:
+    add uniform in [1, 1000]; max, replace and insert uniform in [1, 2^40]
+    per op, so duplicate replace / insert copies of one key carry different
+    values.  Returns (ops u8, keys u64, vals u64)."""
+    ranks = zipf(batch_seed * 1000003 + 11, n_ops, universe, s)
+    keys = rank_to_key(ranks, universe_seed)
+    c20 = (mix13(keys ^ np.uint64(batch_seed & ((1 << 64) - 1))) % np.uint64(20)).astype(np.int64)
+    table = np.array([MX_ADD] * 4 + [MX_MAX] * 2 + [MX_REPLACE] * 2 + [MX_INSERT] * 2 + [MX_QUERY] * 8
+                     + [MX_ERASE] * 2, np.uint8)
+    ops = table[c20]
+    vals = uniform_int(batch_seed + 0x61, n_ops, 1, (1 << 40))
+    add = ops == MX_ADD
+    vals[add] = uniform_int(batch_seed + 0x62, int(add.sum()), 1, 1000)
+    vals[(ops == MX_QUERY) | (ops == MX_ERASE)] = 0
+    return ops, keys, vals
+
+
+def mixed_request_codes(seed: int, n: int, universe: int, universe_seed: int, s: float = 0.99):
+    """A serving request that uses every op code, with results that do not
+    depend on which concurrent copy of a key wins: a key's code is fixed per
+    request by a splitmix64 draw of key ^ seed mod 20 (10 query, 4 add, 2
+    max, 2 replace, 1 insert, 1 erase); every replace and insert copy of one
+    key carries the same value (derived from the key and the request), max
+    values are uniform in [1, 2^40] (max is commutative), add values in
+    [1, 1000].  Returns (ops u8, keys u64, vals u64)."""
+    ranks = zipf(seed * 7 + 3, n, universe, s)
+    keys = rank_to_key(ranks, universe_seed)
+    c20 = (mix13(keys ^ np.uint64(seed & ((1 << 64) - 1))) % np.uint64(20)).astype(np.int64)
+    table = np.array([MX_QUERY] * 10 + [MX_ADD] * 4 + [MX_MAX] * 2 + [MX_REPLACE] * 2 + [MX_INSERT, MX_ERASE],
+                     np.uint8)
+    ops = table[c20]
+    vals = uniform_int(seed + 0x91, n, 1, 1000)
+    mx = ops == MX_MAX
+    vals[mx] = uniform_int(seed + 0x92, int(mx.sum()), 1, 1 << 40)
+    one = (ops == MX_REPLACE) | (ops == MX_INSERT)
+    vals[one] = mix13(keys[one] ^ np.uint64((seed * 0x2545F491) & ((1 << 64) - 1))) % np.uint64(1 << 40) \
+        + np.uint64(1)
+    vals[(ops == MX_QUERY) | (ops == MX_ERASE)] = 0
+    return ops, keys, vals
+
+
 def log_uniform_int(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
     """Integers whose log2 is uniform in [log2 lo, log2 hi] (rounded down)."""
     u = uniform01(seed, n)
