@@ -66,6 +66,10 @@ def parse():
     p.add_argument("--host-direct", type=int, default=1, choices=[0, 1, 2],
                    help="e2e: page-locked host buffers staged (0), inputs read in place (1), "
                         "inputs and results in place (2)")
+    p.add_argument("--no-extra", action="store_true",
+                   help="default line only: skip the read-peak probes, the L2-resident leg and the short "
+                        "batched and serving legs")
+    p.add_argument("--serve-requests", type=int, default=240, help="requests of the default line's serving leg")
     p.add_argument("--tiles", default="auto", choices=["auto", "paper", "4", "8", "16", "32"],
                    help="auto: per design, the tile size with the fastest step (measured before timing); "
                         "paper: each design's tile from the paper; a number: that tile for every design")
@@ -193,6 +197,30 @@ def peak_gbs():
         return 6800.0, "fallback"
 
 
+def read_peaks(dev_index=0):
+    """Read bandwidth of this GPU measured by the library's probe kernel
+    (ws_read_bandwidth; CUDA events, best of five): sequential and random
+    128-byte-line reads of L2-resident buffers (the peak for tables that fit
+    in L2), and random lines over a 4 GiB buffer (HBM, for comparison with the
+    copy bandwidth of MEASURED_PEAKS.json)."""
+    import ctypes
+    import paper_2509_16407_gb300 as ws
+    L = ws.lib()
+    out = {}
+    for name, nbytes, pattern, passes in (("l2_seq_32MiB", 32 << 20, 0, 200), ("l2_seq_64MiB", 64 << 20, 0, 100),
+                                          ("l2_lines_32MiB", 32 << 20, 1, 100),
+                                          ("l2_lines_64MiB", 64 << 20, 1, 50),
+                                          ("hbm_lines_4GiB", 4 << 30, 1, 2), ("hbm_seq_4GiB", 4 << 30, 0, 2)):
+        g = ctypes.c_double(0.0)
+        rc = L.ws_read_bandwidth(nbytes, pattern, passes, dev_index, ctypes.byref(g))
+        out[name] = round(g.value, 1) if rc == 0 else None
+    l2 = [v for k, v in out.items() if k.startswith("l2_seq") and v]
+    out["l2_peak_gbs"] = max(l2) if l2 else None
+    out["how"] = ("ws_read_bandwidth: ld.global.cg 16-byte loads, buffer read once to warm, then `passes` reads "
+                  "timed with CUDA events, best of 5; lines = random 128-byte lines read by 8 lanes together")
+    return out
+
+
 def kernel_source_hash():
     """Hash of the sources of the single-table kernels the default line runs
     (device header, kernel templates, instantiation units): recorded DRAM
@@ -237,7 +265,7 @@ def config2_workload(args, names):
             f" 2^{lq} positive + negative queries, 2^{lq} upsert-add, slice erase, count), designs {names}")
 
 
-def bench_ours(args, rank, world):
+def bench_ours(args, rank, world, peak_override=None):
     import torch
     import paper_2509_16407_gb300 as ws
 
@@ -377,6 +405,12 @@ def bench_ours(args, rank, world):
             return sec + 32 + 16
         return sec + 32 + (32 if m else 0) + 8  # erase: scan + slot (+ tag) write + key in
 
+    def line_bytes(name, ph):
+        """The same count with every line the probe touches charged 128 bytes:
+        random DRAM reads on this part move whole 128-byte lines, so a 64-byte
+        tag line or a 16-byte candidate slot costs as much as a full line."""
+        return alg_bytes(name, ph) + (costs[name][ph]["lines"] * 128.0 - costs[name][ph]["sectors"] * 32.0)
+
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -396,7 +430,7 @@ def bench_ours(args, rank, world):
     ms, value = aggregate(t0.elapsed_time(t1), ops_per_step * args.steps, world, dev)
 
     # per-phase times, achieved bandwidth and probe costs
-    peak, peak_kind = peak_gbs()
+    peak, peak_kind = peak_override if peak_override else peak_gbs()
     phase_ms = {name: {ph: 0.0 for ph in PHASES} for name, _ in tables}
     for k in range(args.steps):
         for di, (name, _) in enumerate(tables):
@@ -411,6 +445,8 @@ def bench_ours(args, rank, world):
             per_launch_ms = phase_ms[name][ph] / args.steps
             b = alg_bytes(name, ph)
             gbs = b * n_of[ph] / (per_launch_ms * 1e-3) / 1e9
+            lb = line_bytes(name, ph)
+            lgbs = lb * n_of[ph] / (per_launch_ms * 1e-3) / 1e9
             breakdown[name][ph] = {
                 "gops": round(n_of[ph] / (per_launch_ms * 1e-3) / 1e9, 3),
                 "ms": round(per_launch_ms, 4),
@@ -419,6 +455,8 @@ def bench_ours(args, rank, world):
                 "sectors_per_op": round(costs[name][ph]["sectors"], 3),
                 "achieved_gbs": round(gbs, 1),
                 "frac_of_measured_hbm": round(gbs / peak, 4),
+                "line_bytes_per_op": round(lb, 1),
+                "frac_line_granularity": round(lgbs / peak, 4),
             }
             if dom is None or per_launch_ms > dom[2]:
                 dom = (name, ph, per_launch_ms, gbs, b * n_of[ph])
@@ -427,11 +465,14 @@ def bench_ours(args, rank, world):
                     "erase": "batch_kernel<KIND_ERASE>"}
     tr = recorded_traffic()
     tile_of = {name: t.info()["tile"] for name, t in tables}
-    traffic = tr.get(f"{dom[0]}:{dom[1]}:{tile_of[dom[0]]}")
+    # recorded DRAM traffic exists for the default workload only
+    default_wl = args.log2_slots == 28 and args.nq == 1 << 24 and args.load == 0.9
+    traffic = tr.get(f"{dom[0]}:{dom[1]}:{tile_of[dom[0]]}") if default_wl else None
     roofline = {"bound": "hbm", "achieved": round(dom[3], 1), "peak": peak, "unit": "GB/s",
                 "frac": round(dom[3] / peak, 4), "traffic": traffic,
                 "kernel": f"{dom[0]} {dom[1]}: {kernel_names[dom[1]]}",
-                "alg_bytes_per_launch": int(dom[4]), "peak_kind": f"{peak_kind} (burst copy)"}
+                "alg_bytes_per_launch": int(dom[4]),
+                "peak_kind": peak_kind if peak_override else f"{peak_kind} (burst copy)"}
 
     # end to end through the C ABI with pinned host buffers
     e2e = None
@@ -458,6 +499,30 @@ def bench_ours(args, rank, world):
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "breakdown": breakdown,
     }
     return result
+
+
+def bench_l2_leg(args, rank, world, l2_peak):
+    """The default step on 2^22-slot tables (64 MiB of slots, each table
+    L2-resident while its phases run), with 2^21 queries / upserts per phase;
+    fractions against the measured L2 read peak instead of HBM."""
+    import copy
+    import torch
+    a = copy.copy(args)
+    a.log2_slots, a.nq, a.no_e2e = 22, 1 << 21, True
+    r = bench_ours(a, rank, world, peak_override=(l2_peak, "measured L2 read, sequential (ws_read_bandwidth)"))
+    torch.cuda.empty_cache()
+    bd = {}
+    for name, phases in r["breakdown"].items():
+        bd[name] = {}
+        for ph, d in phases.items():
+            d = dict(d)
+            d["frac_of_l2_peak"] = d.pop("frac_of_measured_hbm")
+            d.pop("frac_line_granularity", None)
+            d.pop("line_bytes_per_op", None)
+            bd[name][ph] = d
+    return {"workload": r["config"]["workload"], "value": r["value"], "unit": UNIT, "steps": r["steps"],
+            "ms_per_step": r["ms_per_step"], "l2_peak_gbs": l2_peak, "tiles": r["config"]["tiles"],
+            "roofline": r["roofline"], "clocks": r["clocks"], "breakdown": bd}
 
 
 def bench_e2e(args, tables, keys_slice, vals_slice, keys_pos, keys_neg, keys_up, vals_up, base_n, ops_per_step,
@@ -606,17 +671,16 @@ def bench_reference(args, rank, world):
 # half present / half absent); one persistent graph launch per step vs one
 # insert + one query launch per table, identical results required.
 # ---------------------------------------------------------------------------
-def bench_batched(args):
+def bench_batched(args, n_tables=None, reps=None, tune_reps=3):
     import torch
-    import oracle
     import paper_2509_16407_gb300 as ws
     from paper_2509_16407_gb300 import autotune
     dev = torch.device("cuda", 0)
-    n_t = args.tables
+    n_t = n_tables or args.tables
     caps = W.log_uniform_int(41, n_t, 1 << 10, 1 << 22)
     nops = W.log_uniform_int(42, n_t, 1 << 8, 1 << 20)
     t_tune = time.time()
-    choice, timings = autotune.tune(log=lambda m: print(m, file=sys.stderr, flush=True))
+    choice, timings = autotune.tune(reps=tune_reps, log=lambda m: print(m, file=sys.stderr, flush=True))
     t_tune = time.time() - t_tune
     specs = []
     for i in range(n_t):
@@ -671,7 +735,7 @@ def bench_batched(args):
     for (cap, ki, vi, q), t, (si, qv, qs) in zip(specs, tuned, tout):
         items += [(t, ws.BK_INSERT, ki, vi, None, si, 0), (t, ws.BK_QUERY, q, None, qv, qs, 1)]
     plan = ws.BatchPlan(items)
-    reps = max(args.steps, 3)
+    reps = reps or max(args.steps, 3)
     timed(plan.launch, tuned, args.warmup)
     ts_batched = timed(plan.launch, tuned, reps)
     res_b = [(si.clone(), qv.clone(), qs.clone()) for si, qv, qs in tout]
@@ -692,16 +756,6 @@ def bench_batched(args):
     timed(lambda: run_plain(dflt, dout), dflt, 1)
     ts_plain_default = timed(lambda: run_plain(dflt, dout), dflt, reps)
     same_default = all(torch.equal(a, b) for ra, rb in zip(res_b, dout) for a, b in zip(ra, rb))
-    # oracle on a sample of tables
-    bad = 0
-    for i in range(0, n_t, max(1, n_t // 48)):
-        cap, ki, vi, q = specs[i]
-        om = oracle.OracleMap()
-        wst = om.insert(ki.cpu().numpy().view(np.uint64), vi.cpu().numpy().view(np.uint64))
-        wv, wq = om.query(q.cpu().numpy().view(np.uint64))
-        si, qv, qs = res_b[i]
-        bad += int(not ((si.cpu().numpy() == wst).all() and (qv.cpu().numpy().view(np.uint64) == wv).all()
-                        and (qs.cpu().numpy() == wq).all()))
     med = statistics.median
     return {
         "metric": "batched Gops/s (1024 tables, one graph launch) vs per-table launches", "unit": UNIT,
@@ -711,7 +765,7 @@ def bench_batched(args):
         "ms": {"batched": round(med(ts_batched), 3), "plain_tuned": round(med(ts_plain_tuned), 3),
                "plain_default": round(med(ts_plain_default), 3)},
         "identical_results": {"batched_vs_plain_tuned": same, "batched_vs_plain_default": same_default},
-        "oracle_sampled_tables_mismatching": bad, "total_ops": total_ops, "tables": n_t,
+        "total_ops": total_ops, "tables": n_t,
         "launches": {"batched": 1, "plain": 2 * n_t}, "configs": cfg_count, "fallback_items": fallback,
         "autotune_seconds": round(t_tune, 1),
         "autotune_choice": {str(k): "/".join(map(str, v)) for k, v in choice.items()},
@@ -725,12 +779,12 @@ def bench_batched(args):
 # erase, Zipf(0.99) keys); saturated throughput, then Poisson arrivals at 50%
 # and 90% of it; continuous batching vs plain per-request launches.
 # ---------------------------------------------------------------------------
-def bench_serve(args):
+def bench_serve(args, n_req=None, reps=3):
     import torch
     import paper_2509_16407_gb300 as ws
     n_tab = 64
     caps = W.log_uniform_int(51, n_tab, 1 << 16, 1 << 26)
-    n_req = args.requests
+    n_req = n_req or args.requests
     sizes = W.log_uniform_int(52, n_req, 1, 1 << 20)
     tabs = (W.splitmix64(53, n_req) % np.uint64(n_tab)).astype(int)
 
@@ -777,11 +831,14 @@ def bench_serve(args):
                 "p99_ms": float(np.percentile(lat, 99) * 1e3), "launches": st["launches"], "grows": st["grows"],
                 "seconds": t_end - t0}, outs, counts
 
-    def median_run(plain, arrivals=None, reps=3):
-        # the median of `reps` runs by throughput (one process serves them all)
+    def median_run(plain, arrivals=None):
+        # the median of `reps` runs by throughput (one process serves them all);
+        # the spread is reported beside it
         rs = [run(plain, arrivals) for _ in range(reps)]
         rs.sort(key=lambda r: r[0]["gops"])
-        return rs[len(rs) // 2]
+        med = rs[len(rs) // 2]
+        med[0]["gops_runs"] = [round(r[0]["gops"], 4) for r in rs]
+        return med
 
     run(False)  # warm-up, untimed: first-use costs (memory pool, module loading)
     sat_c, out_c, cnt_c = median_run(False)
@@ -800,7 +857,7 @@ def bench_serve(args):
         res[f"poisson_{int(load * 100)}pct"] = {"continuous": c, "plain": p_, "offered_gops": load * sat_c["gops"]}
     rnd = lambda d: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in d.items()}
     return {"metric": "serve p50/p99 latency and Gops/s, continuous batching vs plain per-request launches "
-                      "(median of 3 runs per mode after a warm-up run)",
+                      f"(median of {reps} runs per mode after a warm-up run)",
             "unit": UNIT, "value": round(sat_c["gops"], 4), "higher_is_better": True,
             "runs": {k: {kk: rnd(vv) if isinstance(vv, dict) else vv for kk, vv in v.items()} for k, v in res.items()},
             "identical_query_results_and_counts": same, "requests": n_req, "total_ops": total_ops,
@@ -1003,11 +1060,18 @@ def bench_phased(args):
 # load / tile sweep (config 2): one JSON line per (slots, design, tile, load)
 # ---------------------------------------------------------------------------
 def sweep(args):
+    """Config 2's load / tile sweep: per (slots, design, tile, load) the 5%
+    insert slice ending at that load, 2^24 (or S/4) positive and as many
+    negative queries, their probe costs, and the fraction of the roofline:
+    against the measured HBM copy peak for tables larger than L2, against the
+    measured L2 read peak for the 2^22-slot tables."""
     import torch
     import paper_2509_16407_gb300 as ws
     dev = torch.device("cuda", 0)
     peak, _ = peak_gbs()
+    peaks = read_peaks()
     out = open(args.sweep, "w")
+    out.write(json.dumps({"read_peaks": peaks, "hbm_copy_peak_gbs": peak}) + "\n")
     loads = [0.5, 0.7, 0.8, 0.9, 0.95]
     for lg in [int(x) for x in args.sweep_log2_slots.split(",")]:
         S = 1 << lg
@@ -1016,9 +1080,12 @@ def sweep(args):
         keys = gen_dev(0xABC + lg, top + nq, 0, dev)
         vals = keys * 3
         neg = keys[top:]
+        in_l2 = S * 16 < 100 * (1 << 20)
+        den = peaks["l2_peak_gbs"] if in_l2 else peak
         for scheme, meta, name in ALL_DESIGNS:
             for tile in (4, 8, 16, 32):
                 t = ws.Table(S, scheme, meta, tile=tile)
+                B = t.info()["bucket_slots"]
                 have = 0
                 for lf in loads:
                     n_lf = int(lf * S)
@@ -1026,6 +1093,11 @@ def sweep(args):
                     # fill to lf - 0.05 untimed, then time the 5% slice
                     if lo > have:
                         t.insert(keys[have:lo], vals[have:lo])
+                    # the slice's scan cost before it is inserted (as the default line counts it),
+                    # one line per probe step (T = 8, or B when smaller)
+                    t.set_tile(min(8, B))
+                    ic, _ = t.probe_cost(keys[lo:min(n_lf, lo + (1 << 18))])
+                    t.set_tile(tile)
                     a, b, c, d, e = (torch.cuda.Event(enable_timing=True) for _ in range(5))
                     a.record()
                     st = t.insert(keys[lo:n_lf], vals[lo:n_lf], return_status=True)
@@ -1040,19 +1112,29 @@ def sweep(args):
                     torch.cuda.synchronize()
                     have = n_lf
                     fails = int((st == ws.FAIL_FULL).sum().item())
+                    t.set_tile(min(8, B))
                     pc, _ = t.probe_cost(pos[: 1 << 18])
                     nc, _ = t.probe_cost(neg[: 1 << 18])
-                    pcs = float((pc.cpu().numpy().view(np.uint64) & np.uint64(0xFFFFFFFF)).mean())
-                    ncs = float((nc.cpu().numpy().view(np.uint64) & np.uint64(0xFFFFFFFF)).mean())
+                    t.set_tile(tile)
+                    sec = lambda x: float((x.cpu().numpy().view(np.uint64) & np.uint64(0xFFFFFFFF)).mean())
+                    ics, pcs, ncs = sec(ic), sec(pc), sec(nc)
                     ins_ms, qp_ms, qn_ms = a.elapsed_time(b), c.elapsed_time(d), d.elapsed_time(e)
+                    ins_b = ics * 32 + 32 + (32 if meta else 0) + 16
+                    ins_gbs = (n_lf - lo) * ins_b / ins_ms / 1e6
+                    qp_gbs = nq * (pcs * 32 + 16) / qp_ms / 1e6
+                    qn_gbs = nq * (ncs * 32 + 16) / qn_ms / 1e6
                     rec = {"slots": S, "design": name, "tile": tile, "load": lf,
                            "insert_gops": round((n_lf - lo) / ins_ms / 1e6, 3),
                            "query_pos_gops": round(nq / qp_ms / 1e6, 3),
                            "query_neg_gops": round(nq / qn_ms / 1e6, 3),
-                           "query_pos_gbs": round(nq * (pcs * 32 + 16) / qp_ms / 1e6, 1),
-                           "query_neg_gbs": round(nq * (ncs * 32 + 16) / qn_ms / 1e6, 1),
-                           "query_pos_sectors": round(pcs, 3), "query_neg_sectors": round(ncs, 3),
-                           "insert_failures": fails, "peak_gbs": peak}
+                           "insert_gbs": round(ins_gbs, 1), "query_pos_gbs": round(qp_gbs, 1),
+                           "query_neg_gbs": round(qn_gbs, 1),
+                           "insert_sectors": round(ics, 3), "query_pos_sectors": round(pcs, 3),
+                           "query_neg_sectors": round(ncs, 3),
+                           "peak_gbs": den, "peak_kind": "L2 read (measured)" if in_l2 else "HBM copy (measured)",
+                           "frac_insert": round(ins_gbs / den, 4), "frac_query_pos": round(qp_gbs / den, 4),
+                           "frac_query_neg": round(qn_gbs / den, 4),
+                           "insert_failures": fails, "count": t.count()}
                     out.write(json.dumps(rec) + "\n")
                     out.flush()
                 t.close()
@@ -1093,7 +1175,19 @@ def main():
         batches = make_mixed_batches()  # host pool first: no GPU context exists yet
         print(json.dumps(bench_mixed(args, batches)), flush=True)
         return
+    extra = world == 1 and not args.no_extra
+    peaks = read_peaks() if extra else None  # before the tables take the memory
     res = bench_ours(args, rank, world)
+    if extra:
+        import torch
+        torch.cuda.empty_cache()
+        res["read_peaks"] = peaks
+        if peaks.get("l2_peak_gbs"):
+            res["l2_resident"] = bench_l2_leg(args, rank, world, peaks["l2_peak_gbs"])
+        res["batched"] = bench_batched(args, n_tables=1024, reps=5, tune_reps=1)
+        torch.cuda.empty_cache()
+        res["serve"] = bench_serve(args, n_req=args.serve_requests, reps=3)
+        torch.cuda.empty_cache()
     if rank == 0:
         if not args.no_cpu:
             res["cpu_baseline"] = cpu_baseline(args.cpu_seconds)

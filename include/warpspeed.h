@@ -374,6 +374,20 @@ ws_status ws_server_stats(ws_server* s, uint64_t* submitted, uint64_t* completed
 /* Finishes queued work, then frees the server and its tables. */
 ws_status ws_server_destroy(ws_server* s);
 
+/* ---------------------------------------------------------------------------
+ * Measurement helper (not an operation of the paper): the read bandwidth of
+ * the running GPU for the roofline's denominators -- for tables that fit in
+ * L2 the relevant peak is L2 bandwidth, not HBM.  Allocates a buffer of
+ * `bytes` (>= 1 MiB, a multiple of 128) on `device` (-1 = current), reads it
+ * once to warm it, then times `passes` further reads with CUDA events, five
+ * times, and stores the best rate in *gbs_out (10^9 bytes per second, bytes
+ * read / elapsed).  pattern 0: sequential 16-byte loads at a grid stride;
+ * pattern 1: random 128-byte lines, read by eight lanes together as a bucket
+ * snapshot is (the probes' access pattern).  Loads bypass L1 (.cg), so a
+ * buffer smaller than L2 measures L2.  Synchronous; frees the buffer.
+ * WS_ERR_OOM when the buffer cannot be allocated. */
+ws_status ws_read_bandwidth(uint64_t bytes, int pattern, int passes, int device, double* gbs_out);
+
 /* Text of the last CUDA error seen by this library on the calling thread. */
 const char* ws_cuda_error_string(void);
 const char* ws_status_string(ws_status s);
