@@ -198,26 +198,41 @@ def peak_gbs():
 
 
 def read_peaks(dev_index=0):
-    """Read bandwidth of this GPU measured by the library's probe kernel
-    (ws_read_bandwidth; CUDA events, best of five): sequential and random
-    128-byte-line reads of L2-resident buffers (the peak for tables that fit
-    in L2), and random lines over a 4 GiB buffer (HBM, for comparison with the
-    copy bandwidth of MEASURED_PEAKS.json)."""
+    """Memory rates of this GPU measured by the library's probe kernel
+    (ws_read_bandwidth; CUDA events, best of five): sequential reads of an
+    L2-resident buffer (the peak for tables that fit in L2) and of a 4 GiB
+    buffer, and random 128-, 64- and 32-byte reads and 32- and 128-byte writes
+    over 4 GiB, each at the in-flight depth (1-8 blocks per group of lanes)
+    that runs fastest.  Random accesses per second are the bound of the hash
+    table's probes: every probe step is one random line."""
     import ctypes
     import paper_2509_16407_gb300 as ws
     L = ws.lib()
+
+    def rate(nbytes, pattern, passes, depths=(1, 2, 4, 8)):
+        best, best_d = 0.0, None
+        for d in depths:
+            g = ctypes.c_double(0.0)
+            if L.ws_read_bandwidth(nbytes, pattern, d, passes, dev_index, ctypes.byref(g)) == 0 and g.value > best:
+                best, best_d = g.value, d
+        return round(best, 1), best_d
+
     out = {}
     for name, nbytes, pattern, passes in (("l2_seq_32MiB", 32 << 20, 0, 200), ("l2_seq_64MiB", 64 << 20, 0, 100),
-                                          ("l2_lines_32MiB", 32 << 20, 1, 100),
-                                          ("l2_lines_64MiB", 64 << 20, 1, 50),
-                                          ("hbm_lines_4GiB", 4 << 30, 1, 2), ("hbm_seq_4GiB", 4 << 30, 0, 2)):
-        g = ctypes.c_double(0.0)
-        rc = L.ws_read_bandwidth(nbytes, pattern, passes, dev_index, ctypes.byref(g))
-        out[name] = round(g.value, 1) if rc == 0 else None
-    l2 = [v for k, v in out.items() if k.startswith("l2_seq") and v]
+                                          ("hbm_seq_4GiB", 4 << 30, 0, 2)):
+        out[name] = rate(nbytes, pattern, passes, depths=(1,))[0]
+    out["l2_lines_64MiB"], _ = rate(64 << 20, 1, 50)
+    for name, pattern, w in (("hbm_rand128", 1, 128), ("hbm_rand64", 2, 64), ("hbm_rand32", 3, 32),
+                             ("hbm_wr32", 4, 32), ("hbm_wr128", 5, 128)):
+        gbs, d = rate(4 << 30, pattern, 2)
+        out[name + "_gbs"] = gbs
+        out[name + "_gaccess_s"] = round(gbs / w, 2)
+        out[name + "_depth"] = d
+    l2 = [out[k] for k in ("l2_seq_32MiB", "l2_seq_64MiB") if out.get(k)]
     out["l2_peak_gbs"] = max(l2) if l2 else None
-    out["how"] = ("ws_read_bandwidth: ld.global.cg 16-byte loads, buffer read once to warm, then `passes` reads "
-                  "timed with CUDA events, best of 5; lines = random 128-byte lines read by 8 lanes together")
+    out["how"] = ("ws_read_bandwidth: .cg 16-byte accesses, buffer touched once to warm, then `passes` sweeps "
+                  "timed with CUDA events, best of 5; randN / wrN = random N-byte blocks read / written by N/16 "
+                  "lanes together, best in-flight depth of 1, 2, 4, 8 blocks per group")
     return out
 
 
@@ -265,7 +280,7 @@ def config2_workload(args, names):
             f" 2^{lq} positive + negative queries, 2^{lq} upsert-add, slice erase, count), designs {names}")
 
 
-def bench_ours(args, rank, world, peak_override=None):
+def bench_ours(args, rank, world, peak_override=None, access_peak=None):
     import torch
     import paper_2509_16407_gb300 as ws
 
@@ -447,6 +462,12 @@ def bench_ours(args, rank, world, peak_override=None):
             gbs = b * n_of[ph] / (per_launch_ms * 1e-3) / 1e9
             lb = line_bytes(name, ph)
             lgbs = lb * n_of[ph] / (per_launch_ms * 1e-3) / 1e9
+            # random DRAM accesses per op: every line the probe reads, plus one
+            # write-back per written sector (slot / value, and the tag with metadata)
+            writes = {"insert": 2 if meta_of[name] else 1, "upsert_add": 1,
+                      "erase": 2 if meta_of[name] else 1}.get(ph, 0)
+            acc = costs[name][ph]["lines"] + writes
+            gacc = acc * n_of[ph] / (per_launch_ms * 1e-3) / 1e9
             breakdown[name][ph] = {
                 "gops": round(n_of[ph] / (per_launch_ms * 1e-3) / 1e9, 3),
                 "ms": round(per_launch_ms, 4),
@@ -457,7 +478,11 @@ def bench_ours(args, rank, world, peak_override=None):
                 "frac_of_measured_hbm": round(gbs / peak, 4),
                 "line_bytes_per_op": round(lb, 1),
                 "frac_line_granularity": round(lgbs / peak, 4),
+                "accesses_per_op": round(acc, 3),
+                "gaccess_s": round(gacc, 2),
             }
+            if access_peak:
+                breakdown[name][ph]["frac_of_random_line_rate"] = round(gacc / access_peak, 4)
             if dom is None or per_launch_ms > dom[2]:
                 dom = (name, ph, per_launch_ms, gbs, b * n_of[ph])
     kernel_names = {"insert": "batch_kernel<KIND_UPSERT, op=insert>", "query_pos": "batch_kernel<KIND_QUERY>",
@@ -1177,7 +1202,7 @@ def main():
         return
     extra = world == 1 and not args.no_extra
     peaks = read_peaks() if extra else None  # before the tables take the memory
-    res = bench_ours(args, rank, world)
+    res = bench_ours(args, rank, world, access_peak=peaks["hbm_rand128_gaccess_s"] if peaks else None)
     if extra:
         import torch
         torch.cuda.empty_cache()

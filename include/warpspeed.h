@@ -163,6 +163,12 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  chunks (lane waves, then tiles for what is left), as batched and serving
  *  launches always do, and as insert-if-unique calls on two-choice and
  *  iceberg tables do (their inserts lock: once per chunk beats once per wave).
+ *  Queries and erases on two-choice tables with plain 32-slot buckets read
+ *  whole buckets in 32-op chunks; 2 streams them too, reading a bucket line by
+ *  line up to the key or the first EMPTY slot: fewer bytes for keys near the
+ *  front of b_0, more dependent steps for misses (measured at 2^28 slots, 0.9
+ *  load: positive queries 1.32 vs 1.47 ms, negative queries 3.53 vs 2.57 ms,
+ *  erases 2.27 vs 1.66 ms per 2^24 ops), so it pays only for batches of hits.
  *  WS_OPT_LANE_WAVES (double hashing only; 0..255, 0 = default): buckets of a
  *  probe sequence the lane path follows, one per wave, before an op still
  *  open goes to the tiles.  Default: the whole sequence when streaming, 4 in
@@ -381,12 +387,18 @@ ws_status ws_server_destroy(ws_server* s);
  * `bytes` (>= 1 MiB, a multiple of 128) on `device` (-1 = current), reads it
  * once to warm it, then times `passes` further reads with CUDA events, five
  * times, and stores the best rate in *gbs_out (10^9 bytes per second, bytes
- * read / elapsed).  pattern 0: sequential 16-byte loads at a grid stride;
- * pattern 1: random 128-byte lines, read by eight lanes together as a bucket
- * snapshot is (the probes' access pattern).  Loads bypass L1 (.cg), so a
- * buffer smaller than L2 measures L2.  Synchronous; frees the buffer.
- * WS_ERR_OOM when the buffer cannot be allocated. */
-ws_status ws_read_bandwidth(uint64_t bytes, int pattern, int passes, int device, double* gbs_out);
+ * moved / elapsed).  pattern 0: sequential 16-byte loads at a grid stride;
+ * 1, 2, 3: random 128-, 64- and 32-byte blocks, each read by 8, 4 or 2 lanes
+ * together as a bucket snapshot is (the probes' access pattern); 4, 5: random
+ * 32- and 128-byte blocks written; 6, 7: a metadata probe's pair of dependent
+ * reads, a random 64-byte tag line then a 16-byte slot chosen from its data,
+ * with tags and slots in separate arrays (6) or each bucket's tag line and 32
+ * slots in one 640-byte block (7), rated at 80 bytes per pair.  depth (1, 2,
+ * 4 or 8): independent random blocks (pairs) each group of lanes keeps in
+ * flight (ignored by pattern 0; 6 and 7 run 2 or 4).  Accesses
+ * bypass L1 (.cg), so a buffer smaller than L2 measures L2.  Synchronous;
+ * frees the buffer.  WS_ERR_OOM when the buffer cannot be allocated. */
+ws_status ws_read_bandwidth(uint64_t bytes, int pattern, int depth, int passes, int device, double* gbs_out);
 
 /* Text of the last CUDA error seen by this library on the calling thread. */
 const char* ws_cuda_error_string(void);

@@ -156,9 +156,11 @@ class Table:
         """Double hashing: buckets the lane path follows before the tiles (0 = default)."""
         _check(lib().ws_set_option(self._h, 3, int(n)), "ws_set_option")
 
-    def set_stream(self, on: bool):
-        """Streaming lanes in single-table calls (on by default) or 32-op chunks."""
-        _check(lib().ws_set_option(self._h, 4, int(bool(on))), "ws_set_option")
+    def set_stream(self, on):
+        """Streaming lanes in single-table calls (True / 1, the default) or 32-op
+        chunks (False / 0); 2 also streams plain two-choice queries and erases
+        line by line instead of reading whole buckets."""
+        _check(lib().ws_set_option(self._h, 4, int(on)), "ws_set_option")
 
     def set_host_direct(self, mode: int):
         """Page-locked host buffers: 0 staged, 1 inputs read in place, 2 results written in place too."""

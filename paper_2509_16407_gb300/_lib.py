@@ -98,7 +98,7 @@ SIGNATURES = {
     "ws_server_stats": (st, [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                              ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
     "ws_server_destroy": (st, [vp]),
-    "ws_read_bandwidth": (st, [u64, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]),
+    "ws_read_bandwidth": (st, [u64, i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]),
     "ws_cuda_error_string": (ctypes.c_char_p, []),
     "ws_status_string": (ctypes.c_char_p, [i32]),
     "ws_version": (u32, []),

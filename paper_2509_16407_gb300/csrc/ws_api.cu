@@ -464,7 +464,7 @@ ws_status ws_set_option(ws_table* t, int option, int64_t value) {
       t->tv.lane_waves = (int)value;
       return WS_OK;
     case WS_OPT_STREAM:
-      if (value != 0 && value != 1) return WS_ERR_INVALID;
+      if (value < 0 || value > 2) return WS_ERR_INVALID;
       t->tv.stream = (int)value;
       return WS_OK;
     case WS_OPT_HOST_DIRECT:

@@ -1853,7 +1853,9 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
   // lines, positive queries 1.51 vs 1.31, upserts 1.87 vs 1.66).
   constexpr bool kRounds = (SCHEME == SCHEME_P2) && !META && B == 32;
   const bool lock_bound = (KIND == KIND_UPSERT) && SCHEME != SCHEME_DOUBLE && a.op == OP_INSERT;
-  const bool rounds = kRounds && (KIND == KIND_QUERY || KIND == KIND_ERASE);
+  // (WS_OPT_STREAM = 2 streams them too, by lines: fewer bytes for hits near
+  // the front of b_0, more dependent steps for misses.)
+  const bool rounds = kRounds && (KIND == KIND_QUERY || KIND == KIND_ERASE) && tv.stream != 2;
   if (!tv.stream || lock_bound || rounds) {
     // 32-op chunks, grid-stride
     const u64 nchunks = (a.n + 31) / 32;

@@ -1,8 +1,9 @@
 """Every way a single-table call can be served gives the oracle's results:
-streaming lanes (the default), 32-op chunks (WS_OPT_STREAM = 0), a capped
-lane path (WS_OPT_LANE_WAVES), and tiles only (WS_OPT_PRELOAD = 0), on every
-design and on two-choice tables with 16-slot buckets (lanes that read a
-bucket line by line).  Needs a GPU."""
+streaming lanes (the default), 32-op chunks (WS_OPT_STREAM = 0), streaming
+lanes also for plain two-choice queries and erases (WS_OPT_STREAM = 2, by
+lines instead of whole buckets), a capped lane path (WS_OPT_LANE_WAVES), and
+tiles only (WS_OPT_PRELOAD = 0), on every design and on two-choice tables with
+16-slot buckets (lanes that read a bucket line by line).  Needs a GPU."""
 import numpy as np
 import pytest
 
@@ -12,7 +13,7 @@ from tests._gpu import DESIGNS, DESIGN_IDS, check_layout, dev, host
 pytestmark = pytest.mark.gpu
 
 MODES = {"stream": dict(), "chunks": dict(stream=False), "lanes2": dict(lane_waves=2),
-         "tiles": dict(preload=False)}
+         "tiles": dict(preload=False), "stream_lines": dict(stream=2)}
 CASES = [(s, m, 0) for s, m in DESIGNS] + [("p2", False, 16)]
 CASE_IDS = DESIGN_IDS + ["P2HT-B16"]
 
