@@ -63,9 +63,10 @@ def parse():
                    help="config2 = the default line; batched = 1024 uneven tables in one graph launch")
     p.add_argument("--tables", type=int, default=1024)
     p.add_argument("--requests", type=int, default=600, help="serve: requests per run")
-    p.add_argument("--host-direct", type=int, default=1, choices=[0, 1, 2],
+    p.add_argument("--host-direct", type=int, default=3, choices=[0, 1, 2, 3],
                    help="e2e: page-locked host buffers staged (0), inputs read in place (1), "
-                        "inputs and results in place (2)")
+                        "inputs and results in place (2), in place for inserts and erases and staged "
+                        "otherwise (3, the library's default)")
     p.add_argument("--no-extra", action="store_true",
                    help="default line only: skip the read-peak probes, the L2-resident leg and the short "
                         "batched and serving legs")
@@ -526,15 +527,19 @@ def bench_ours(args, rank, world, peak_override=None, access_peak=None):
     return result
 
 
-def bench_l2_leg(args, rank, world, l2_peak):
+def bench_l2_leg(args, rank, world, peaks):
     """The default step on 2^22-slot tables (64 MiB of slots, each table
-    L2-resident while its phases run), with 2^21 queries / upserts per phase;
-    fractions against the measured L2 read peak instead of HBM."""
+    L2-resident while its phases run) with the same 2^24 queries / upserts per
+    phase; fractions against the measured L2 read peak instead of HBM, and
+    random-line rates against the measured rate of random 128-byte L2 reads."""
     import copy
     import torch
     a = copy.copy(args)
-    a.log2_slots, a.nq, a.no_e2e = 22, 1 << 21, True
-    r = bench_ours(a, rank, world, peak_override=(l2_peak, "measured L2 read, sequential (ws_read_bandwidth)"))
+    a.log2_slots, a.no_e2e = 22, True
+    l2_peak = peaks["l2_peak_gbs"]
+    lines = peaks.get("l2_lines_64MiB")
+    r = bench_ours(a, rank, world, peak_override=(l2_peak, "measured L2 read, sequential (ws_read_bandwidth)"),
+                   access_peak=lines / 128.0 if lines else None)
     torch.cuda.empty_cache()
     bd = {}
     for name, phases in r["breakdown"].items():
@@ -544,9 +549,12 @@ def bench_l2_leg(args, rank, world, l2_peak):
             d["frac_of_l2_peak"] = d.pop("frac_of_measured_hbm")
             d.pop("frac_line_granularity", None)
             d.pop("line_bytes_per_op", None)
+            if "frac_of_random_line_rate" in d:
+                d["frac_of_l2_random_line_rate"] = d.pop("frac_of_random_line_rate")
             bd[name][ph] = d
     return {"workload": r["config"]["workload"], "value": r["value"], "unit": UNIT, "steps": r["steps"],
-            "ms_per_step": r["ms_per_step"], "l2_peak_gbs": l2_peak, "tiles": r["config"]["tiles"],
+            "ms_per_step": r["ms_per_step"], "l2_peak_gbs": l2_peak, "l2_random_line_gbs": lines,
+            "tiles": r["config"]["tiles"],
             "roofline": r["roofline"], "clocks": r["clocks"], "breakdown": bd}
 
 
@@ -590,7 +598,9 @@ def bench_e2e(args, tables, keys_slice, vals_slice, keys_pos, keys_neg, keys_up,
     return {"value": round(e2e_value, 4), "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "host_buffers": ["staged through device chunks", "inputs read in place, results staged",
-                             "read and written in place"][args.host_direct]}
+                             "read and written in place",
+                             "inputs read in place by inserts and erases, staged for queries and upserts; "
+                             "results staged"][args.host_direct]}
 
 
 # ---------------------------------------------------------------------------
@@ -1086,8 +1096,8 @@ def bench_phased(args):
 # ---------------------------------------------------------------------------
 def sweep(args):
     """Config 2's load / tile sweep: per (slots, design, tile, load) the 5%
-    insert slice ending at that load, 2^24 (or S/4) positive and as many
-    negative queries, their probe costs, and the fraction of the roofline:
+    insert slice ending at that load, 2^24 positive and as many negative
+    queries, their probe costs, and the fraction of the roofline:
     against the measured HBM copy peak for tables larger than L2, against the
     measured L2 read peak for the 2^22-slot tables."""
     import torch
@@ -1100,7 +1110,7 @@ def sweep(args):
     loads = [0.5, 0.7, 0.8, 0.9, 0.95]
     for lg in [int(x) for x in args.sweep_log2_slots.split(",")]:
         S = 1 << lg
-        nq = min(1 << 24, S // 4)
+        nq = 1 << 24  # 2^24 positive and 2^24 negative queries at every size
         top = int(0.95 * S)
         keys = gen_dev(0xABC + lg, top + nq, 0, dev)
         vals = keys * 3
@@ -1208,7 +1218,7 @@ def main():
         torch.cuda.empty_cache()
         res["read_peaks"] = peaks
         if peaks.get("l2_peak_gbs"):
-            res["l2_resident"] = bench_l2_leg(args, rank, world, peaks["l2_peak_gbs"])
+            res["l2_resident"] = bench_l2_leg(args, rank, world, peaks)
         res["batched"] = bench_batched(args, n_tables=1024, reps=5, tune_reps=1)
         torch.cuda.empty_cache()
         res["serve"] = bench_serve(args, n_req=args.serve_requests, reps=3)

@@ -25,7 +25,8 @@
  *  Batch buffers (keys, vals, ops, outputs) may be DEVICE pointers on the
  *  table's device (the fast path: kernels read them in place) or HOST pointers
  *  (pinned or pageable): the library then streams them through internal device
- *  staging buffers in chunks, overlapping copies with the kernels, and the
+ *  staging buffers in chunks, overlapping copies with the kernels (see
+ *  WS_OPT_HOST_DIRECT and WS_OPT_STAGE_CHUNK), and the
  *  outputs land in host memory once `stream` completes.  Buffers must be
  *  8-byte aligned (u64 arrays) and stay valid until `stream` completes.  The
  *  caller owns all batch buffers; the table owns its slot, tag, lock and
@@ -173,20 +174,29 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  probe sequence the lane path follows, one per wave, before an op still
  *  open goes to the tiles.  Default: the whole sequence when streaming, 4 in
  *  32-op chunks. */
-/*  WS_OPT_HOST_DIRECT (0..2, default 1): what a call does with host
+/*  WS_OPT_HOST_DIRECT (0..3, default 3): what a call does with host
  *  buffers that are page-locked and mapped into the device's address space
  *  (cudaHostAlloc / cudaMallocHost / cudaHostRegister memory with unified
  *  addressing).  0: every host buffer is staged through the table's device
- *  chunks (copy engines, double-buffered against the kernels).  1: the
- *  kernels read keys, values and op codes in place over the host link; host
- *  result buffers are still staged.  2: results are written in place too.
- *  Pageable host memory is always staged.  The caller must not touch the
- *  buffers until the call's work on its stream has completed.  Measured on
- *  a GB300 with its Grace host (2^28-slot tables, the four designs' insert /
- *  query / upsert / erase step with pinned buffers): 7.9 Gops/s staged, 9.2
- *  with inputs in place, 6.8 with results written in place as well (scattered
- *  small writes over the host link cost more than one bulk copy). */
-enum { WS_OPT_PRELOAD = 1, WS_OPT_PHASED = 2, WS_OPT_LANE_WAVES = 3, WS_OPT_STREAM = 4, WS_OPT_HOST_DIRECT = 5 };
+ *  chunks (copy engines, four chunk buffers rotating against the kernels).
+ *  1: the kernels read keys, values and op codes in place over the host
+ *  link; host result buffers are still staged.  2: results are written in
+ *  place too.  3: 1 for insert-if-unique and erase calls (their probe
+ *  sequences hide the host link's latency), 0 for queries, upserts and mixed
+ *  batches (whose kernels are short per op and read inputs faster from
+ *  device memory).  Pageable host memory is always staged.  The caller must
+ *  not touch the buffers until the call's work on its stream has completed.
+ *  Measured on a GB300 with its Grace host (2^28-slot tables, insert / query
+ *  / upsert / erase of 13.4M / 2^24 ops per phase, four designs): the step
+ *  takes 27.2 ms with device buffers, about 34 ms with inputs read in place,
+ *  33 staged, 30.5 automatic; results written in place cost most (scattered
+ *  small writes over the host link). */
+/*  WS_OPT_STAGE_CHUNK (16..24, default 21): log2 of the ops per chunk of the
+ *  staging pipeline for host buffers (four rotating chunk buffers per table,
+ *  allocated at the first host-buffer call; changing the size synchronises
+ *  the table's last stream and frees them). */
+enum { WS_OPT_PRELOAD = 1, WS_OPT_PHASED = 2, WS_OPT_LANE_WAVES = 3, WS_OPT_STREAM = 4, WS_OPT_HOST_DIRECT = 5,
+       WS_OPT_STAGE_CHUNK = 6 };
 ws_status ws_set_option(ws_table* t, int option, int64_t value);
 
 /* Insert-if-unique (§5.1 Upsert with the empty callback).  status_out: per-op
@@ -393,9 +403,12 @@ ws_status ws_server_destroy(ws_server* s);
  * 32- and 128-byte blocks written; 6, 7: a metadata probe's pair of dependent
  * reads, a random 64-byte tag line then a 16-byte slot chosen from its data,
  * with tags and slots in separate arrays (6) or each bucket's tag line and 32
- * slots in one 640-byte block (7), rated at 80 bytes per pair.  depth (1, 2,
- * 4 or 8): independent random blocks (pairs) each group of lanes keeps in
- * flight (ignored by pattern 0; 6 and 7 run 2 or 4).  Accesses
+ * slots in one 640-byte block (7), rated at 80 bytes per pair; 8-11: random
+ * 128-byte reads confined to regions of 128 KiB, 512 KiB, 2 MiB or 8 MiB, each
+ * block of threads reading 8 x depth lines per group of lanes in one region
+ * before it moves to another.  depth (1, 2, 4 or 8): independent random
+ * blocks (pairs) each group of lanes keeps in flight (ignored by pattern 0; 6
+ * and 7 run 2 or 4).  Accesses
  * bypass L1 (.cg), so a buffer smaller than L2 measures L2.  Synchronous;
  * frees the buffer.  WS_ERR_OOM when the buffer cannot be allocated. */
 ws_status ws_read_bandwidth(uint64_t bytes, int pattern, int depth, int passes, int device, double* gbs_out);

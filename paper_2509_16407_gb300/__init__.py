@@ -162,8 +162,13 @@ class Table:
         line by line instead of reading whole buckets."""
         _check(lib().ws_set_option(self._h, 4, int(on)), "ws_set_option")
 
+    def set_stage_chunk(self, log2_ops: int):
+        """Ops per chunk of the host-buffer staging pipeline, as a power of two (16..24)."""
+        _check(lib().ws_set_option(self._h, 6, int(log2_ops)), "ws_set_option")
+
     def set_host_direct(self, mode: int):
-        """Page-locked host buffers: 0 staged, 1 inputs read in place, 2 results written in place too."""
+        """Page-locked host buffers: 0 staged, 1 inputs read in place, 2 results written in place too,
+        3 (default) in place for inserts and erases, staged for the other calls."""
         _check(lib().ws_set_option(self._h, 5, int(mode)), "ws_set_option")
 
     def clear(self, stream=None):

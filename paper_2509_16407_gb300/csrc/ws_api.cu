@@ -27,7 +27,6 @@ constexpr u64 kSeed1 = 0x243f6a8885a308d3ull;  // hex digits of pi: fixed, docum
 constexpr u64 kSeed2 = 0x13198a2e03707344ull;
 constexpr uint32_t kDefaultProbe = 80;
 constexpr uint32_t kDefaultSpin = 1u << 16;  // attempts; each costs a probe + <= 1 us back-off
-constexpr u64 kStageOps = 1ull << 22;  // ops per staging chunk (host-buffer path)
 constexpr int kDefaultPreload = 1;  // the lane path (see WS_OPT_PRELOAD)
 
 }  // namespace
@@ -35,7 +34,7 @@ constexpr int kDefaultPreload = 1;  // the lane path (see WS_OPT_PRELOAD)
 namespace {
 
 void free_staging(Staging* s) {
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < Staging::kBufs; ++b) {
     if (s->keys[b]) cudaFree(s->keys[b]);
     if (s->vals[b]) cudaFree(s->vals[b]);
     if (s->out[b]) cudaFree(s->out[b]);
@@ -71,9 +70,9 @@ ws_status ensure_staging(ws_table* t) {
   if (t->stage) return WS_OK;
   Staging* s = new (std::nothrow) Staging();
   if (!s) return WS_ERR_OOM;
-  s->cap = kStageOps;
+  s->cap = 1ull << t->stage_log2;
   bool ok = true;
-  for (int b = 0; b < 2 && ok; ++b) {
+  for (int b = 0; b < Staging::kBufs && ok; ++b) {
     ok = cudaMalloc(&s->keys[b], s->cap * 8) == cudaSuccess && cudaMalloc(&s->vals[b], s->cap * 8) == cudaSuccess &&
          cudaMalloc(&s->out[b], s->cap * 8) == cudaSuccess && cudaMalloc(&s->ops[b], s->cap) == cudaSuccess &&
          cudaMalloc(&s->st[b], s->cap) == cudaSuccess;
@@ -176,12 +175,18 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
   tv.shortcut = t->never_erased;
   t->last_stream = s;
 
-  if (t->host_direct >= 1) {  // inputs read in place
+  // WS_OPT_HOST_DIRECT 3 (automatic): page-locked inputs are read in place
+  // by calls whose kernels spend long per op (insert-if-unique, erase: the
+  // host link's latency hides behind their probe sequences) and staged
+  // through the copy engines for the others (queries, upserts, mixed).
+  int hd = t->host_direct;
+  if (hd == 3) hd = (kind == ws::KIND_ERASE || (kind == ws::KIND_UPSERT && op == ws::OP_INSERT)) ? 1 : 0;
+  if (hd >= 1) {  // inputs read in place
     go_direct(keys, pk);
     go_direct(vals, pv);
     go_direct(ops, po);
   }
-  if (t->host_direct >= 2) {  // results written in place
+  if (hd >= 2) {  // results written in place
     go_direct(vals_out, pvo);
     go_direct(status_out, pst);
   }
@@ -199,7 +204,7 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
   u64 chunk = 0;
   for (u64 off = 0; off < n; off += g.cap, ++chunk) {
     const u64 m = (n - off) < g.cap ? (n - off) : g.cap;
-    const int b = (int)(chunk & 1);
+    const int b = (int)(chunk % Staging::kBufs);
     WS_CUDA(cudaStreamWaitEvent(g.h2d, g.k_done[b], 0));
     const u64* kp = keys + off;
     const u64* vp = vals ? vals + off : nullptr;
@@ -231,10 +236,8 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
       WS_CUDA(cudaEventRecord(g.out_done[b], g.d2h));
     }
   }
-  if (host_out) {
-    WS_CUDA(cudaStreamWaitEvent(s, g.out_done[0], 0));
-    WS_CUDA(cudaStreamWaitEvent(s, g.out_done[1], 0));
-  }
+  if (host_out)
+    for (int b = 0; b < Staging::kBufs && (u64)b < chunk; ++b) WS_CUDA(cudaStreamWaitEvent(s, g.out_done[b], 0));
   return WS_OK;
 }
 
@@ -467,8 +470,18 @@ ws_status ws_set_option(ws_table* t, int option, int64_t value) {
       if (value < 0 || value > 2) return WS_ERR_INVALID;
       t->tv.stream = (int)value;
       return WS_OK;
+    case WS_OPT_STAGE_CHUNK:
+      if (value < 16 || value > 24) return WS_ERR_INVALID;
+      if (t->stage && t->stage->cap != (1ull << value)) {  // reallocated at the next host-buffer call
+        DeviceGuard guard(t->device);
+        WS_CUDA(cudaStreamSynchronize(t->last_stream));
+        free_staging(t->stage);
+        t->stage = nullptr;
+      }
+      t->stage_log2 = (int)value;
+      return WS_OK;
     case WS_OPT_HOST_DIRECT:
-      if (value < 0 || value > 2) return WS_ERR_INVALID;
+      if (value < 0 || value > 3) return WS_ERR_INVALID;
       t->host_direct = (int)value;
       return WS_OK;
   }

@@ -12,18 +12,20 @@ using ws::u64;
 using ws::u8;
 using ws::u32;
 
-// Double-buffered staging for host batch buffers: H2D copies on one stream,
-// kernels on the caller's stream, D2H copies on a third, chained by events.
+// Staging for host batch buffers: kBufs rotating chunk buffers, H2D copies on
+// one stream, kernels on the caller's stream, D2H copies on a third, chained
+// by events, so the copies of later chunks run while earlier chunks' kernels
+// do.
 struct Staging {
-  u64 cap = 0;
-  u64* keys[2] = {nullptr, nullptr};
-  u64* vals[2] = {nullptr, nullptr};
-  u64* out[2] = {nullptr, nullptr};
-  u8* ops[2] = {nullptr, nullptr};
-  u8* st[2] = {nullptr, nullptr};
+  static constexpr int kBufs = 4;
+  u64 cap = 0;  // ops per chunk
+  u64* keys[kBufs] = {};
+  u64* vals[kBufs] = {};
+  u64* out[kBufs] = {};
+  u8* ops[kBufs] = {};
+  u8* st[kBufs] = {};
   cudaStream_t h2d = nullptr, d2h = nullptr;
-  cudaEvent_t in_ready[2] = {nullptr, nullptr}, k_done[2] = {nullptr, nullptr},
-              out_done[2] = {nullptr, nullptr};
+  cudaEvent_t in_ready[kBufs] = {}, k_done[kBufs] = {}, out_done[kBufs] = {};
 };
 
 void note_cuda(cudaError_t e, const char* where);
@@ -61,7 +63,8 @@ struct ws_table {
   int T = 0, scheme = 0, meta = 0, device = 0, num_sms = 0;
   uint32_t pmax = 0, spin = 0;
   int never_erased = 1;
-  int host_direct = 1;  // WS_OPT_HOST_DIRECT
+  int host_direct = 3;  // WS_OPT_HOST_DIRECT (3: automatic)
+  int stage_log2 = 22;  // WS_OPT_STAGE_CHUNK: ops per staging chunk, log2
   wsi::u64 bytes = 0;
   cudaStream_t last_stream = nullptr;
   wsi::Staging* stage = nullptr;

@@ -16,7 +16,10 @@
 //   6, 7 a metadata probe's dependent pair of reads -- a 64-byte tag line,
 //     then one 16-byte slot chosen from the tag data -- with the tags in a
 //     separate array (6, the tables' layout) or each bucket's tag line and
-//     slots in one 640-byte block (7, a co-located layout).
+//     slots in one 640-byte block (7, a co-located layout);
+//   8-11 random 128-byte reads confined to regions of 128 KiB, 512 KiB,
+//     2 MiB or 8 MiB: each block of threads reads 8 x depth random lines
+//     per group in one region, then moves to another.
 // With a buffer smaller than L2 the second pass onwards is served by L2.
 #include <cstdio>
 
@@ -134,6 +137,35 @@ __global__ void __launch_bounds__(256) tag_then_slot(uint4* __restrict__ p, uint
   if (acc == 0x9e3779b9u) atomicAdd(sink, 1u);
 }
 
+// Random 128-byte reads confined to regions: every block of threads works
+// in one region of `region_lines` lines at a time (its groups of eight lanes
+// read random lines of it, `per_region` lines each), then moves to another
+// random region -- the access pattern of a batch processed partition by
+// partition when partitions follow the table's address order.
+__global__ void __launch_bounds__(256) regional_lines(uint4* __restrict__ p, uint64_t n_lines, uint64_t region_lines,
+                                                     int steps, int per_region, int passes, unsigned int* sink) {
+  uint32_t acc = 0;
+  const uint64_t groups = ((uint64_t)gridDim.x * blockDim.x) / 8;
+  const uint64_t group = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) / 8;
+  const int part = threadIdx.x % 8;
+  const uint64_t n_regions = n_lines / region_lines;
+  for (int r = 0; r < passes; ++r) {
+    const uint64_t ctr = ((uint64_t)r * groups + group) * (uint64_t)steps;
+    for (int s = 0; s < steps; s += 4) {
+      const uint64_t epoch = ((uint64_t)r * (uint64_t)steps + (uint64_t)s) / (uint64_t)per_region;
+      const uint64_t reg = ((mix(((uint64_t)blockIdx.x << 32) ^ epoch ^ 0x5bd1e995ull) >> 32) * n_regions) >> 32;
+      uint64_t l[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        l[k] = reg * region_lines + (((mix(ctr + (uint64_t)(s + k)) >> 32) * region_lines) >> 32);
+      const uint4 a = ld_cg16(p + l[0] * 8 + part), b = ld_cg16(p + l[1] * 8 + part),
+                  c = ld_cg16(p + l[2] * 8 + part), d = ld_cg16(p + l[3] * 8 + part);
+      acc ^= a.x ^ b.y ^ c.z ^ d.w;
+    }
+  }
+  if (acc == 0x9e3779b9u) atomicAdd(sink, 1u);
+}
+
 template <int LPG, bool WRITE>
 void launch_random(int depth, int grid, uint4* q, uint64_t n_blocks, int steps, int np, unsigned int* sink) {
   switch (depth) {
@@ -148,7 +180,7 @@ void launch_random(int depth, int grid, uint4* q, uint64_t n_blocks, int steps, 
 
 extern "C" ws_status ws_read_bandwidth(uint64_t bytes, int pattern, int depth, int passes, int device,
                                        double* gbs_out) {
-  if (!gbs_out || bytes < (1u << 20) || (bytes & 127u) || passes < 1 || pattern < 0 || pattern > 7 ||
+  if (!gbs_out || bytes < (1u << 20) || (bytes & 127u) || passes < 1 || pattern < 0 || pattern > 11 ||
       (depth != 1 && depth != 2 && depth != 4 && depth != 8))
     return WS_ERR_INVALID;
   int dev = device;
@@ -175,10 +207,10 @@ extern "C" ws_status ws_read_bandwidth(uint64_t bytes, int pattern, int depth, i
   // group of eight lanes of the line pattern reads `steps` lines per pass
   const int grid = 8 * sms;
   // random patterns: 1 = 128-byte reads, 2 = 64-byte, 3 = 32-byte, 4 = 32-byte writes, 5 = 128-byte writes
-  const int lpg = (pattern == 1 || pattern == 5) ? 8 : (pattern == 2 || pattern >= 6) ? 4 : 2;
+  const int lpg = (pattern == 1 || pattern == 5 || pattern >= 8) ? 8 : (pattern == 2 || pattern >= 6) ? 4 : 2;
   // patterns 6, 7: buckets of 640 bytes (a tag line and 32 slots, plus
   // spare), counted as the 80 bytes a probe pair reads
-  const uint64_t block_bytes = pattern >= 6 ? 640 : 16ull * (uint64_t)lpg;
+  const uint64_t block_bytes = (pattern == 6 || pattern == 7) ? 640 : 16ull * (uint64_t)lpg;
   const uint64_t n_blocks = bytes / block_bytes;
   const uint64_t groups = (uint64_t)grid * 256 / (uint64_t)lpg;
   const int steps = (int)(((n_blocks + groups - 1) / groups + 7) / 8 * 8);  // a multiple of every depth
@@ -195,10 +227,16 @@ extern "C" ws_status ws_read_bandwidth(uint64_t bytes, int pattern, int depth, i
         if (depth <= 2) tag_then_slot<true, 2><<<grid, 256>>>(q, n_blocks, steps, np, sink);
         else tag_then_slot<true, 4><<<grid, 256>>>(q, n_blocks, steps, np, sink);
         break;
-      default:
+      case 7:
         if (depth <= 2) tag_then_slot<false, 2><<<grid, 256>>>(q, n_blocks, steps, np, sink);
         else tag_then_slot<false, 4><<<grid, 256>>>(q, n_blocks, steps, np, sink);
         break;
+      default: {  // 8..11: regions of 2^(10 + 2 (pattern - 8)) lines: 128 KiB, 512 KiB, 2 MiB, 8 MiB
+        const uint64_t rl = 1ull << (10 + 2 * (pattern - 8));
+        if (rl > n_blocks) return cudaErrorInvalidValue;
+        regional_lines<<<grid, 256>>>(q, n_blocks, rl, steps, 8 * depth, np, sink);
+        break;
+      }
     }
     return cudaGetLastError();
   };
@@ -219,7 +257,7 @@ extern "C" ws_status ws_read_bandwidth(uint64_t bytes, int pattern, int depth, i
         rc = WS_ERR_CUDA;
         break;
       }
-      const double per = pattern >= 6 ? 80.0 : (double)block_bytes;  // a probe pair reads 64 + 16 bytes
+      const double per = (pattern == 6 || pattern == 7) ? 80.0 : (double)block_bytes;  // a pair reads 64 + 16 bytes
       const double read = pattern == 0 ? (double)n16 * 16.0 : (double)groups * (double)steps * per;
       const float gbs = (float)(read * passes / (ms * 1e-3) / 1e9);
       if (gbs > best) best = gbs;

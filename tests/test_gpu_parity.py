@@ -463,9 +463,10 @@ def test_rehash_into_larger_table(ws, oracle_mod, scheme, meta):
 
 # --------------------------------------------------------------------------
 # page-locked host buffers: staged (0), read in place (1), read and written
-# in place (2) -- every mode gives the oracle's results
+# in place (2), in place or staged by op kind (3) -- every mode gives the
+# oracle's results
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("scheme,meta", DESIGNS, ids=DESIGN_IDS)
 def test_host_direct_matches_oracle(ws, oracle_mod, scheme, meta, mode):
     import torch
