@@ -63,10 +63,10 @@ def parse():
                    help="config2 = the default line; batched = 1024 uneven tables in one graph launch")
     p.add_argument("--tables", type=int, default=1024)
     p.add_argument("--requests", type=int, default=600, help="serve: requests per run")
-    p.add_argument("--host-direct", type=int, default=3, choices=[0, 1, 2, 3],
-                   help="e2e: page-locked host buffers staged (0), inputs read in place (1), "
-                        "inputs and results in place (2), in place for inserts and erases and staged "
-                        "otherwise (3, the library's default)")
+    p.add_argument("--host-direct", type=int, default=1, choices=[0, 1, 2, 3],
+                   help="e2e: page-locked host buffers staged (0), inputs read in place (1, the library's "
+                        "default), inputs and results in place (2), in place for inserts and erases and "
+                        "staged otherwise (3)")
     p.add_argument("--no-extra", action="store_true",
                    help="default line only: skip the read-peak probes, the L2-resident leg and the short "
                         "batched and serving legs")

@@ -174,7 +174,7 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  probe sequence the lane path follows, one per wave, before an op still
  *  open goes to the tiles.  Default: the whole sequence when streaming, 4 in
  *  32-op chunks. */
-/*  WS_OPT_HOST_DIRECT (0..3, default 3): what a call does with host
+/*  WS_OPT_HOST_DIRECT (0..3, default 1): what a call does with host
  *  buffers that are page-locked and mapped into the device's address space
  *  (cudaHostAlloc / cudaMallocHost / cudaHostRegister memory with unified
  *  addressing).  0: every host buffer is staged through the table's device
@@ -187,10 +187,14 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  device memory).  Pageable host memory is always staged.  The caller must
  *  not touch the buffers until the call's work on its stream has completed.
  *  Measured on a GB300 with its Grace host (2^28-slot tables, insert / query
- *  / upsert / erase of 13.4M / 2^24 ops per phase, four designs): the step
- *  takes 27.2 ms with device buffers, about 34 ms with inputs read in place,
- *  33 staged, 30.5 automatic; results written in place cost most (scattered
- *  small writes over the host link). */
+ *  / upsert / erase of 13.4M / 2^24 ops per call, four designs, copies at
+ *  about 200 GB/s each way): calls issued back to back run fastest with
+ *  inputs read in place (9.26 Gops/s against 8.4-9.0 automatic and 8.6
+ *  staged; device buffers 11.3), because staged copies then overlap the
+ *  previous calls' kernels and compete with their memory traffic; calls
+ *  timed one at a time run fastest automatic (a step of 30.2 ms against 34.0
+ *  in place).  Results written in place cost most (scattered small writes
+ *  over the host link). */
 /*  WS_OPT_STAGE_CHUNK (16..24, default 21): log2 of the ops per chunk of the
  *  staging pipeline for host buffers (four rotating chunk buffers per table,
  *  allocated at the first host-buffer call; changing the size synchronises

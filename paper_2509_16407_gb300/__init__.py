@@ -167,8 +167,8 @@ class Table:
         _check(lib().ws_set_option(self._h, 6, int(log2_ops)), "ws_set_option")
 
     def set_host_direct(self, mode: int):
-        """Page-locked host buffers: 0 staged, 1 inputs read in place, 2 results written in place too,
-        3 (default) in place for inserts and erases, staged for the other calls."""
+        """Page-locked host buffers: 0 staged, 1 (default) inputs read in place, 2 results written in
+        place too, 3 in place for inserts and erases and staged for the other calls."""
         _check(lib().ws_set_option(self._h, 5, int(mode)), "ws_set_option")
 
     def clear(self, stream=None):

@@ -63,7 +63,7 @@ struct ws_table {
   int T = 0, scheme = 0, meta = 0, device = 0, num_sms = 0;
   uint32_t pmax = 0, spin = 0;
   int never_erased = 1;
-  int host_direct = 3;  // WS_OPT_HOST_DIRECT (3: automatic)
+  int host_direct = 1;  // WS_OPT_HOST_DIRECT
   int stage_log2 = 22;  // WS_OPT_STAGE_CHUNK: ops per staging chunk, log2
   wsi::u64 bytes = 0;
   cudaStream_t last_stream = nullptr;
