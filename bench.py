@@ -254,9 +254,11 @@ def kernel_source_hash():
 
 def recorded_traffic():
     """Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of
-    each design:phase:tile kernel at the default workload, from the committed
-    ncu summary; empty when the kernels changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", "dram_traffic_2p28.txt")
+    each design:phase kernel of the default workload, from the committed ncu
+    summary (measured on 2^26-slot tables and scaled by the ops per launch,
+    which grow 4x to 2^28; the tile changes them by under 2%); empty when the
+    kernels changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_config2.txt")
     out, src = {}, None
     try:
         with open(path) as f:
@@ -264,7 +266,7 @@ def recorded_traffic():
                 ln = ln.split("#", 1)[0].split()
                 if len(ln) == 2 and ln[0] == "source_hash":
                     src = ln[1]
-                elif len(ln) == 2 and ln[0].count(":") == 2:  # design:phase:tile bytes
+                elif len(ln) == 2 and ln[0].count(":") == 1:  # design:phase bytes
                     out[ln[0]] = float(ln[1])
     except OSError:
         return {}
@@ -493,7 +495,7 @@ def bench_ours(args, rank, world, peak_override=None, access_peak=None):
     tile_of = {name: t.info()["tile"] for name, t in tables}
     # recorded DRAM traffic exists for the default workload only
     default_wl = args.log2_slots == 28 and args.nq == 1 << 24 and args.load == 0.9
-    traffic = tr.get(f"{dom[0]}:{dom[1]}:{tile_of[dom[0]]}") if default_wl else None
+    traffic = tr.get(f"{dom[0]}:{dom[1]}") if default_wl else None
     roofline = {"bound": "hbm", "achieved": round(dom[3], 1), "peak": peak, "unit": "GB/s",
                 "frac": round(dom[3] / peak, 4), "traffic": traffic,
                 "kernel": f"{dom[0]} {dom[1]}: {kernel_names[dom[1]]}",
