@@ -43,7 +43,9 @@ struct Counters {
   u64 n_full;     // inserts that found no free slot
   u64 n_timeout;  // ops that hit the lock spin limit
   u64 n_badkey;   // ops on sentinel keys / unknown op codes
-  u64 pad[4];
+  u64 ticket;     // work ticket of the running single-table launch
+  u64 done;       // blocks of that launch that finished; the last one zeroes both
+  u64 pad[2];
 };
 
 // What a kernel needs of a table, passed by value.

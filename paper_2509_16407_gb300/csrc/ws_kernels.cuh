@@ -4,13 +4,13 @@
 // its probe sequence one bucket (or one 128-byte line) per wave, from a
 // snapshot that the warp copies into shared memory with cp.async -- four ops'
 // lines per copy instruction, so up to 32 probes of a warp are in flight per
-// wave.  Single-table calls run "streaming lanes": a warp serves a
-// contiguous share of the batch and a lane takes the next op as soon as its
-// op settles.  What a lane cannot settle alone goes to cooperative tiles of
-// T lanes (T in {4, 8, 16, 32}, §3.2 / §5), which read a bucket in steps of
-// T consecutive 16-byte slots and decide with warp votes, identically on all
-// lanes of the tile: several tag matches, a lost CAS, an insert without the
-// lock, the probe-count kernel.
+// wave.  Single-table calls run "streaming lanes": a warp serves shares of
+// the batch that it takes from a per-launch ticket, and a lane takes the
+// next op as soon as its op settles.  What a lane cannot settle alone goes to
+// cooperative tiles of T lanes (T in {4, 8, 16, 32}, §3.2 / §5), which read
+// a bucket in steps of T consecutive 16-byte slots and decide with warp
+// votes, identically on all lanes of the tile: several tag matches, a lost
+// CAS, an insert without the lock, the probe-count kernel.
 //
 // Probe schemes (§2.2):
 //   double hashing  b_i = (h1 + i * (h2 | 1)) mod nb, i < max_probe; a scan
@@ -1631,9 +1631,14 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
 // no lane of the warp holds a bucket lock a tile might wait for.  Refill
 // pauses once enough ops are parked to fill the tiles.
 // -------------------------------------------------------------------------
+// Work shares: with `ticket` null the warp serves [begin, end); otherwise it
+// takes shares of `share` ops from the launch's ticket (begin / end unused)
+// whenever its lanes run dry, so warps whose ops probe long keep fewer ops
+// and all finish close together.
 template <int SCHEME, bool META, int B, int T, int KIND>
 __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs& a, int upsert_op, bool lockfree,
-                                           u64 begin, u64 end, WarpSmem& sm, int lane) {
+                                           u64 begin, u64 end, WarpSmem& sm, int lane, u64* ticket = nullptr,
+                                           u64 share = 0) {
   using Ops = TileOps<SCHEME, META, B, T>;
   enum { L_EMPTY = 0, L_ACTIVE = 1, L_PARKED = 2 };
   constexpr int NT = 32 / T;
@@ -1652,10 +1657,23 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
   typename Ops::LaneState ls;
   int dcount = 0, tile_d = 0;
   u64 next = begin;
+  bool exhausted = ticket == nullptr;  // no more shares to take
+  if (ticket) next = end = 0;
   for (;;) {
     // 1. refill: empty lanes take the next ops of the range, in lane order
     unsigned parked = __ballot_sync(kAll, state == L_PARKED);
     const unsigned empty = __ballot_sync(kAll, state == L_EMPTY);
+    if (!exhausted && empty && next >= end) {  // the share is used up: take the next one
+      u64 first = 0;
+      if (lane == 0) first = atomicAdd((unsigned long long*)ticket, 1ull) * share;
+      first = __shfl_sync(kAll, first, 0);
+      if (first < a.n) {
+        next = first;
+        end = (a.n - first < share) ? a.n : first + share;
+      } else {
+        exhausted = true;
+      }
+    }
     if (empty && next < end && __popc(parked) < NT) {
       const u64 rank = (u64)__popc(empty & ((1u << lane) - 1u));
       if (state == L_EMPTY && next + rank < end) {
@@ -1826,12 +1844,15 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
       }
       __syncwarp();
       if (state == L_PARKED) state = L_EMPTY;
-    } else if (!any_active && next >= end) {
+    } else if (!any_active && next >= end && exhausted) {
       break;  // nothing active, parked or left to take
     }
   }
   return dcount + tile_d;
 }
+
+constexpr u64 kChunkGroup = 4;     // 32-op chunks a warp takes per ticket
+constexpr u64 kStreamShare = 256;  // ops a streaming warp takes per ticket
 
 template <int SCHEME, bool META, int B, int T, int KIND>
 __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchArgs a) {
@@ -1856,32 +1877,51 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
   // (WS_OPT_STREAM = 2 streams them too, by lines: fewer bytes for hits near
   // the front of b_0, more dependent steps for misses.)
   const bool rounds = kRounds && (KIND == KIND_QUERY || KIND == KIND_ERASE) && tv.stream != 2;
+  // Work comes from the launch's ticket: warps that draw long probe
+  // sequences take less of it.  Shares shrink with the batch so that a small
+  // launch still spreads over every warp (about four shares per warp, 32 to
+  // kStreamShare ops each; one to kChunkGroup chunks).
+  u64* ticket = &tv.ctr->ticket;
+  const u64 warps = (u64)gridDim.x * kWarps;
   if (!tv.stream || lock_bound || rounds) {
-    // 32-op chunks, grid-stride
     const u64 nchunks = (a.n + 31) / 32;
-    const u64 stride = (u64)gridDim.x * kWarps;
-    for (u64 ch = (u64)blockIdx.x * kWarps + w; ch < nchunks; ch += stride)
-      dcount += warp_chunk<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, ch * 32, s_w[w], lane);
-  } else {
-    // streaming lanes: each warp takes an equal contiguous share of the batch
-    const u64 warps = (u64)gridDim.x * kWarps;
-    const u64 per = ((a.n + warps - 1) / warps + 31) / 32 * 32;
-    const u64 begin = ((u64)blockIdx.x * kWarps + w) * per;
-    if (begin < a.n) {
-      const u64 end = (a.n - begin < per) ? a.n : begin + per;
-      dcount += warp_stream<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, begin, end, s_w[w], lane);
+    u64 group = nchunks / (4 * warps);
+    group = group < 1 ? 1 : (group > kChunkGroup ? kChunkGroup : group);
+    for (;;) {
+      u64 c0 = 0;
+      if (lane == 0) c0 = atomicAdd((unsigned long long*)ticket, (unsigned long long)group);
+      c0 = __shfl_sync(0xffffffffu, c0, 0);
+      if (c0 >= nchunks) break;
+      const u64 c1 = (nchunks - c0 < group) ? nchunks : c0 + group;
+      for (u64 ch = c0; ch < c1; ++ch)
+        dcount += warp_chunk<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, ch * 32, s_w[w], lane);
     }
+  } else {
+    u64 share = (a.n / (4 * warps) + 31) / 32 * 32;
+    share = share < 32 ? 32 : (share > kStreamShare ? kStreamShare : share);
+    dcount += warp_stream<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, 0, 0, s_w[w], lane, ticket, share);
   }
   if (KIND != KIND_QUERY && KIND != KIND_PROBE) {
     const int mine = __reduce_add_sync(0xffffffffu, dcount);
     if (lane == 0 && mine) atomicAdd((unsigned long long*)&s_cnt, (unsigned long long)(long long)mine);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_cnt) atomicAdd((unsigned long long*)&tv.ctr->count, (unsigned long long)s_cnt);
+  }
+  __syncthreads();  // every warp of the block is done with the ticket
+  if (threadIdx.x == 0) {
+    if ((KIND != KIND_QUERY && KIND != KIND_PROBE) && s_cnt)
+      atomicAdd((unsigned long long*)&tv.ctr->count, (unsigned long long)s_cnt);
+    // the launch's last block returns the ticket to zero for the next launch
+    // on this table (launches on one table are stream-ordered)
+    __threadfence();
+    if (atomicAdd((unsigned long long*)&tv.ctr->done, 1ull) == (unsigned long long)gridDim.x - 1) {
+      atomicExch((unsigned long long*)&tv.ctr->ticket, 0ull);
+      atomicExch((unsigned long long*)&tv.ctr->done, 0ull);
+    }
   }
 }
 
-// Occupancy-sized grid-stride launch.  The kernel is a template argument so
-// each instantiation caches its own occupancy.
+// Occupancy-sized launch (one full wave of blocks; the warps take their work
+// from the table's ticket).  The kernel is a template argument so each
+// instantiation caches its own occupancy.
 template <void (*KERN)(TableView, BatchArgs)>
 cudaError_t launch_sized(const TableView& tv, const BatchArgs& a, cudaStream_t s, int num_sms) {
   static int occ = 0;
