@@ -1373,106 +1373,124 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
     // Whole-bucket rounds: eight buckets per round, one op's bucket per copy
     // instruction (lane s copies slot s), each scanned with two votes.
     // Pass 0 reads b_0 of every open op, pass 1 b_1 of the ops still open;
-    // the lane owning an op settles it, and hands it to the tiles after a
-    // lost CAS or when it must insert without the lock.
-    bool open = lane_ok && !done;
-    u32 occ0 = 0;
-    int f0 = -1;
-    u64 f0k = 0, f0v = 0;
-    for (u32 c = 0; c < 2; ++c) {
-      const unsigned om = __ballot_sync(0xffffffffu, open);
-      if (!om) break;
-      if (open) {
-        sm.bw[lane] = Ops::bucket(tv, h1, h2, c);
-        sm.list[__popc(om & ((1u << lane) - 1u))] = (u8)lane;
+    // the lane owning an op settles it.  An op that proved its key absent
+    // without holding b_0's lock (its one attempt found the lock taken, or
+    // an add / max / replace that probed lock-free) tries the lock once more
+    // after the rounds and, holding it, reads its buckets again (now in L2)
+    // and claims; only ops that still miss the lock, or lose a CAS, go to
+    // the tiles.
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      bool open = lane_ok && !done;
+      if (attempt == 1) {
+        const bool retry = open && kLaneLock && opk == Ops::LW_UPDATE_ONLY && fresh;
+        const bool got = retry && Ops::lane_lock(tv, b0);
+        if (got) {
+          locked = true;
+          opk = Ops::LW_INSERT_LOCKED;
+        }
+        open = got;
+        if (!__any_sync(0xffffffffu, open)) break;
       }
-      __syncwarp();
-      const int n = __popc(om);
-      int hs = -1, fs = -1;
-      u32 occ = 0;
-      u64 hv = 0, fk = 0, fv = 0;
-      for (int r0 = 0; r0 < n; r0 += 8) {
-        const int nr = (n - r0) < 8 ? (n - r0) : 8;
-#pragma unroll
-        for (int q = 0; q < 8; ++q)
-          if (q < nr) ptx::cp_async16(&sm.pre.flat(q, lane), tv.slots + sm.bw[sm.list[r0 + q]] * 32 + (u64)lane);
-        ptx::cp_async_wait_all();
+      u32 occ0 = 0;
+      int f0 = -1;
+      u64 f0k = 0, f0v = 0;
+      for (u32 c = 0; c < 2; ++c) {
+        const unsigned om = __ballot_sync(0xffffffffu, open);
+        if (!om) break;
+        if (open) {
+          sm.bw[lane] = Ops::bucket(tv, h1, h2, c);
+          sm.list[__popc(om & ((1u << lane) - 1u))] = (u8)lane;
+        }
         __syncwarp();
+        const int n = __popc(om);
+        int hs = -1, fs = -1;
+        u32 occ = 0;
+        u64 hv = 0, fk = 0, fv = 0;
+        for (int r0 = 0; r0 < n; r0 += 8) {
+          const int nr = (n - r0) < 8 ? (n - r0) : 8;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (q >= nr) break;  // warp-uniform
-          const int j = sm.list[r0 + q];
-          const u64 k = sm.pre.flat(q, lane).key;
-          const unsigned mk = __ballot_sync(0xffffffffu, k == sm.key[j]);
-          const unsigned mf = __ballot_sync(0xffffffffu, k == KEY_EMPTY || k == KEY_TOMB);
-          if (lane == j) {
-            occ = 32u - (u32)__popc(mf);
-            if (mk) {
-              hs = __ffs(mk) - 1;
-              hv = sm.pre.flat(q, hs).val;
-            }
-            if (mf) {
-              fs = __ffs(mf) - 1;
-              const Slot f = sm.pre.flat(q, fs);
-              fk = f.key;
-              fv = f.val;
+          for (int q = 0; q < 8; ++q)
+            if (q < nr) ptx::cp_async16(&sm.pre.flat(q, lane), tv.slots + sm.bw[sm.list[r0 + q]] * 32 + (u64)lane);
+          ptx::cp_async_wait_all();
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            if (q >= nr) break;  // warp-uniform
+            const int j = sm.list[r0 + q];
+            const u64 k = sm.pre.flat(q, lane).key;
+            const unsigned mk = __ballot_sync(0xffffffffu, k == sm.key[j]);
+            const unsigned mf = __ballot_sync(0xffffffffu, k == KEY_EMPTY || k == KEY_TOMB);
+            if (lane == j) {
+              occ = 32u - (u32)__popc(mf);
+              if (mk) {
+                hs = __ffs(mk) - 1;
+                hv = sm.pre.flat(q, hs).val;
+              }
+              if (mf) {
+                fs = __ffs(mf) - 1;
+                const Slot f = sm.pre.flat(q, fs);
+                fk = f.key;
+                fv = f.val;
+              }
             }
           }
+          __syncwarp();  // the next round overwrites the rows
         }
-        __syncwarp();  // the next round overwrites the rows
-      }
-      if (!open) continue;
-      const u64 bc = sm.bw[lane];
-      bool absent = false;
-      if (hs >= 0) {
-        const u64 idx = bc * 32 + (u64)hs;
-        open = false;
-        if (opk == Ops::LW_QUERY) {
-          out = hv;
-          st = ST_FOUND;
-          done = true;
-        } else if (opk == Ops::LW_ERASE) {
-          if (ptx::cas_slot(tv.slots + idx, K, hv, KEY_TOMB, 0)) {
+        if (!open) continue;
+        const u64 bc = sm.bw[lane];
+        bool absent = false;
+        if (hs >= 0) {
+          const u64 idx = bc * 32 + (u64)hs;
+          open = false;
+          if (opk == Ops::LW_QUERY) {
             out = hv;
-            --dcount;
+            st = ST_FOUND;
+            done = true;
+          } else if (opk == Ops::LW_ERASE) {
+            if (ptx::cas_slot(tv.slots + idx, K, hv, KEY_TOMB, 0)) {
+              out = hv;
+              --dcount;
+              st = ST_FOUND;
+              done = true;
+            }
+          } else {
+            Ops::apply(tv, idx, op, V);
             st = ST_FOUND;
             done = true;
           }
+        } else if (c == 0) {
+          occ0 = occ;
+          f0 = fs;
+          f0k = fk;
+          f0v = fv;
+          absent = Ops::nprobe(tv) == 1 || (tv.shortcut && occ < Ops::FILL_SHORTCUT);
         } else {
-          Ops::apply(tv, idx, op, V);
-          st = ST_FOUND;
-          done = true;
+          absent = true;
         }
-      } else if (c == 0) {
-        occ0 = occ;
-        f0 = fs;
-        f0k = fk;
-        f0v = fv;
-        absent = Ops::nprobe(tv) == 1 || (tv.shortcut && occ < Ops::FILL_SHORTCUT);
-      } else {
-        absent = true;
-      }
-      if (absent) {
-        open = false;
-        if (opk == Ops::LW_QUERY || opk == Ops::LW_ERASE) {
-          out = 0;
-          st = ST_MISS;
-          done = true;
-        } else if (opk == Ops::LW_INSERT_LOCKED) {
-          const int ch = Ops::p2_choice(occ0, f0 >= 0, occ, fs >= 0, c == 1);
-          if (ch < 0) {
-            st = ST_FULL;
+        if (absent) {
+          open = false;
+          if (opk == Ops::LW_QUERY || opk == Ops::LW_ERASE) {
+            out = 0;
+            st = ST_MISS;
             done = true;
-          } else {
-            const u64 idx = ch == 0 ? b0 * 32 + (u64)f0 : bc * 32 + (u64)fs;
-            if (ptx::cas_slot(tv.slots + idx, ch == 0 ? f0k : fk, ch == 0 ? f0v : fv, K, V)) {
-              ++dcount;
-              st = ST_INSERTED;
+          } else if (opk == Ops::LW_INSERT_LOCKED) {
+            const int ch = Ops::p2_choice(occ0, f0 >= 0, occ, fs >= 0, c == 1);
+            if (ch < 0) {
+              st = ST_FULL;
               done = true;
+            } else {
+              const u64 idx = ch == 0 ? b0 * 32 + (u64)f0 : bc * 32 + (u64)fs;
+              if (ptx::cas_slot(tv.slots + idx, ch == 0 ? f0k : fk, ch == 0 ? f0v : fv, K, V)) {
+                ++dcount;
+                st = ST_INSERTED;
+                done = true;
+              }
             }
           }
         }
       }
+      if (locked && !tv.phased) Ops::lane_unlock(tv, b0, done && st == ST_INSERTED);  // after the claim
+      locked = false;
     }
   }
 
