@@ -181,18 +181,22 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
   // through the copy engines for the others (queries, upserts, mixed).
   int hd = t->host_direct;
   if (hd == 3) hd = (kind == ws::KIND_ERASE || (kind == ws::KIND_UPSERT && op == ws::OP_INSERT)) ? 1 : 0;
+  const int pk0 = pk, pv0 = pv;
   if (hd >= 1) {  // inputs read in place
     go_direct(keys, pk);
     go_direct(vals, pv);
     go_direct(ops, po);
   }
+  // keys (and values) read in place from host memory
+  const bool host_in = (pk0 == PTR_HOST && pk != PTR_HOST) && (vals == nullptr || (pv0 == PTR_HOST && pv != PTR_HOST));
+  const u32 in_flags = host_in ? (u32)ws::BATCH_HOST_INPUTS : 0u;
   if (hd >= 2) {  // results written in place
     go_direct(vals_out, pvo);
     go_direct(status_out, pst);
   }
   const bool any_host = pk == PTR_HOST || pv == PTR_HOST || po == PTR_HOST || pvo == PTR_HOST || pst == PTR_HOST;
   if (!any_host) {
-    ws::BatchArgs a{keys, vals, ops, vals_out, status_out, n, op, 1, 0};
+    ws::BatchArgs a{keys, vals, ops, vals_out, status_out, n, op, 1, in_flags};
     WS_CUDA(dispatch(t, tv, a, kind, s));
     return WS_OK;
   }
@@ -226,7 +230,7 @@ ws_status run_batch(ws_table* t, int kind, int op, const u8* ops, const uint64_t
     WS_CUDA(cudaStreamWaitEvent(s, g.out_done[b], 0));
     u64* vo = vals_out ? (pvo == PTR_HOST ? g.out[b] : vals_out + off) : nullptr;
     u8* so = status_out ? (pst == PTR_HOST ? g.st[b] : status_out + off) : nullptr;
-    ws::BatchArgs a{kp, vp, op_p, vo, so, m, op, 1, 0};
+    ws::BatchArgs a{kp, vp, op_p, vo, so, m, op, 1, in_flags};
     WS_CUDA(dispatch(t, tv, a, kind, s));
     WS_CUDA(cudaEventRecord(g.k_done[b], s));
     if (host_out) {

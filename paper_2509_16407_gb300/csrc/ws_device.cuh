@@ -76,9 +76,14 @@ struct BatchArgs {
   u64 n;
   int op;          // upsert callback for KIND_UPSERT
   u32 key_stride;  // elements between consecutive keys / values (0 or 1: dense; 2: a slot array)
-  u32 flags;       // BATCH_SKIP_SENTINELS: sentinel keys are skipped silently (rehash of a slot array)
+  u32 flags;       // BATCH_SKIP_SENTINELS, BATCH_HOST_INPUTS
 };
-enum { BATCH_SKIP_SENTINELS = 1 };
+// BATCH_SKIP_SENTINELS: sentinel keys are skipped silently (rehash of a slot
+// array).  BATCH_HOST_INPUTS: keys and values are page-locked host memory
+// read in place over the host link; streaming warps then copy each lane's
+// next inputs into shared memory a wave ahead (cp.async), so the link's
+// latency does not hold up the warp's waves.
+enum { BATCH_SKIP_SENTINELS = 1, BATCH_HOST_INPUTS = 2 };
 
 // -------------------------------------------------------------------------
 // Hashing.  The paper does not fix its hash functions; this build uses the
@@ -217,6 +222,12 @@ __device__ __forceinline__ void st_u64_relaxed(u64* p, u64 v) {
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   const u32 d = (u32)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+// 8-byte asynchronous global -> shared copy (cp.async.ca: the .cg form
+// copies 16 bytes only); used to fetch batch inputs a wave ahead.
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const u32 d = (u32)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");

@@ -1291,6 +1291,7 @@ struct WarpSmem {
   u64 key[32], val[32], out[32], h1[32], h2[32];
   u64 bw[32];  // bucket of each op in the current wave
   u8 op[32], st[32], fresh[32], list[32];  // list: open ops of a bucket pass
+  u64 in_key[32], in_val[32];  // streaming lanes, host inputs: op i's key / value in slot i % 32
   PreWarp pre;
 };
 
@@ -1677,6 +1678,13 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
   u64 next = begin;
   bool exhausted = ticket == nullptr;  // no more shares to take
   if (ticket) next = end = 0;
+  // Input ring (host inputs read in place): slot s of in_key / in_val holds
+  // the op i with i % 32 == s among the 32 ops from `next` on (shares start
+  // at multiples of 32).  Lane s copies its slot's op when the share begins
+  // and whenever its op is taken, so a lane that takes a new op finds its
+  // inputs in shared memory: the copies complete during the wave between.
+  const bool ring = (a.flags & BATCH_HOST_INPUTS) != 0 && ticket != nullptr;
+  const bool want_v = (KIND == KIND_UPSERT || KIND == KIND_MIXED) && a.vals != nullptr;
   for (;;) {
     // 1. refill: empty lanes take the next ops of the range, in lane order
     unsigned parked = __ballot_sync(kAll, state == L_PARKED);
@@ -1688,16 +1696,24 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
       if (first < a.n) {
         next = first;
         end = (a.n - first < share) ? a.n : first + share;
+        if (ring && first + (u64)lane < end) {
+          ptx::cp_async8(&sm.in_key[lane], a.keys + (first + lane) * ks);
+          if (want_v) ptx::cp_async8(&sm.in_val[lane], a.vals + (first + lane) * ks);
+        }
       } else {
         exhausted = true;
       }
     }
     if (empty && next < end && __popc(parked) < NT) {
       const u64 rank = (u64)__popc(empty & ((1u << lane) - 1u));
+      if (ring) {  // the ring's copies (usually complete long ago) become visible to the warp
+        ptx::cp_async_wait_all();
+        __syncwarp();
+      }
       if (state == L_EMPTY && next + rank < end) {
         const u64 gi = next + rank;
-        const u64 K = a.keys[gi * ks];
-        const u64 V = ((KIND == KIND_UPSERT || KIND == KIND_MIXED) && a.vals) ? a.vals[gi * ks] : 0;
+        const u64 K = ring ? sm.in_key[gi & 31u] : a.keys[gi * ks];
+        const u64 V = want_v ? (ring ? sm.in_val[gi & 31u] : a.vals[gi * ks]) : 0;
         const u8 code = (KIND == KIND_MIXED) ? a.ops[gi] : 0;
         const u64 h1 = fmix64(K ^ tv.seed1), h2 = fmix64(K ^ tv.seed2);
         u8 st = ST_MISS;
@@ -1753,7 +1769,17 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
         }
       }
       const u64 took = (u64)__popc(empty);
-      next = (end - next < took) ? end : next + took;
+      const u64 ncons = (end - next < took) ? end - next : took;
+      if (ring) {
+        // the slots of the ops just taken receive the op 32 further on
+        __syncwarp();  // every lane has read its slot
+        const u64 off = ((u64)lane - next) & 31u;  // this lane's slot in the window from `next`
+        if (off < ncons && next + off + 32 < end) {
+          ptx::cp_async8(&sm.in_key[lane], a.keys + (next + off + 32) * ks);
+          if (want_v) ptx::cp_async8(&sm.in_val[lane], a.vals + (next + off + 32) * ks);
+        }
+      }
+      next += ncons;
     }
     // 2. one wave: copy each active lane's current bucket, then settle
     const unsigned act = __ballot_sync(kAll, state == L_ACTIVE);
