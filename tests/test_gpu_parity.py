@@ -497,3 +497,37 @@ def test_host_direct_matches_oracle(ws, oracle_mod, scheme, meta, mode):
     assert t.count() == om.count()
     check_layout(oracle_mod, t, om.count())
     t.close()
+
+
+# --------------------------------------------------------------------------
+# work tickets: every single-table launch takes its work from a per-table
+# ticket that the launch's last block returns to zero; back-to-back launches
+# of sizes around a share (1 op ... a few shares, streaming and chunked
+# kernels, every kind) must each see a fresh ticket
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme,meta", DESIGNS, ids=DESIGN_IDS)
+def test_back_to_back_launches_of_every_size(ws, oracle_mod, scheme, meta):
+    t = ws.Table(1 << 16, scheme, meta)
+    om = oracle_mod.OracleMap()
+    keys = W.distinct_keys(5150, 30000)
+    pos = 0
+    sizes = [1, 2, 31, 32, 33, 255, 256, 257, 1000, 4097, 9000]
+    for i, n in enumerate(sizes):
+        k = keys[pos:pos + n]
+        pos += n
+        st = host(t.insert(dev(k), dev(k), return_status=True))
+        assert (st == om.insert(k, k)).all(), n
+        q = keys[max(0, pos - 2 * n):pos + n]
+        v, s = t.query(dev(q), return_status=True)
+        wv, wsx = om.query(q)
+        assert (host(v) == wv).all() and (host(s) == wsx).all(), n
+        u = k[: max(1, n // 2)]
+        ust = host(t.upsert(dev(u), dev(np.ones(u.size, np.uint64)), op="add", return_status=True))
+        assert (ust == om.upsert(u, np.ones(u.size, np.uint64), 0)).all(), n
+        if i % 2:
+            e = k[::3]
+            ev, es = t.erase(dev(e), return_values=True, return_status=True)
+            wv, wsx = om.erase(e)
+            assert (host(ev) == wv).all() and (host(es) == wsx).all(), n
+        assert t.count() == om.count(), n
+    check_layout(oracle_mod, t, om.count())
