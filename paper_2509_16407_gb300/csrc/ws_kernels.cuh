@@ -1286,6 +1286,7 @@ __device__ __forceinline__ void count_failure(const TableView& tv, u8 st) {
 // -------------------------------------------------------------------------
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kLaneRestarts = 2;  // streaming lane: restarts of an op after a lost CAS before the tiles
 
 struct WarpSmem {
   u64 key[32], val[32], out[32], h1[32], h2[32];
@@ -1673,6 +1674,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
   int opk = -1, op = upsert_op;
   bool locked = false, fresh = true;
   u32 w = 0;
+  int restarts = 0;  // restarts of the current op after a lost CAS
   typename Ops::LaneState ls;
   int dcount = 0, tile_d = 0;
   u64 next = begin;
@@ -1750,6 +1752,7 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           sm.out[lane] = gi;  // the op's index
           w = 0;
           fresh = true;
+          restarts = 0;
           ls.ff_set = false;
           ls.ff_idx = ls.ff_k = ls.ff_v = 0;
           ls.occ0 = ls.occ1 = ls.cur_occ = ls.next_w = 0;
@@ -1833,6 +1836,20 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
           // sequence again from b_0 and insert from what it reads
           locked = true;
           opk = Ops::LW_INSERT_LOCKED;
+          w = 0;
+          ls.ff_set = false;
+          ls.ff_idx = ls.ff_k = ls.ff_v = 0;
+          ls.occ0 = ls.occ1 = ls.cur_occ = ls.next_w = 0;
+          ls.f1_set = false;
+          ls.tsum = 0;
+          ls.f1_idx = ls.f1_k = ls.f1_v = 0;
+        } else if (r == -1 && !fresh && restarts < kLaneRestarts) {
+          // a lost CAS: the table moved under the snapshot (another claim
+          // or erase in this bucket).  Follow the sequence again from b_0
+          // -- its lines are in L2 now -- instead of handing the op to a
+          // tile; a held lock stays held.
+          ++restarts;
+          fresh = true;
           w = 0;
           ls.ff_set = false;
           ls.ff_idx = ls.ff_k = ls.ff_v = 0;
