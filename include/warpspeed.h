@@ -196,7 +196,7 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  timed one at a time run fastest automatic (a step of 30.2 ms against 34.0
  *  in place).  Results written in place cost most (scattered small writes
  *  over the host link). */
-/*  WS_OPT_STAGE_CHUNK (16..24, default 21): log2 of the ops per chunk of the
+/*  WS_OPT_STAGE_CHUNK (16..24, default 22): log2 of the ops per chunk of the
  *  staging pipeline for host buffers (four rotating chunk buffers per table,
  *  allocated at the first host-buffer call; changing the size synchronises
  *  the table's last stream and frees them). */

@@ -464,7 +464,8 @@ def test_rehash_into_larger_table(ws, oracle_mod, scheme, meta):
 # --------------------------------------------------------------------------
 # page-locked host buffers: staged (0), read in place (1), read and written
 # in place (2), in place or staged by op kind (3) -- every mode gives the
-# oracle's results
+# oracle's results; staging chunks of 2^16 ops, so the calls that stage
+# run through several chunks and the four rotating buffers
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("scheme,meta", DESIGNS, ids=DESIGN_IDS)
@@ -472,6 +473,7 @@ def test_host_direct_matches_oracle(ws, oracle_mod, scheme, meta, mode):
     import torch
     t = ws.Table(1 << 18, scheme, meta)
     t.set_host_direct(mode)
+    t.set_stage_chunk(16)
     S = t.info()["slots"]
     n = int(0.8 * S)
     both = W.distinct_keys(909 + mode, n + n // 4)
