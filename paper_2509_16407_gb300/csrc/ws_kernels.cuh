@@ -1652,13 +1652,14 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
 // pauses once enough ops are parked to fill the tiles.
 // -------------------------------------------------------------------------
 // Work shares: with `ticket` null the warp serves [begin, end); otherwise it
-// takes shares of `share` ops from the launch's ticket (begin / end unused)
-// whenever its lanes run dry, so warps whose ops probe long keep fewer ops
-// and all finish close together.
+// takes shares of up to `share` ops (a multiple of 32) from the launch's
+// ticket, which counts ops (begin / end unused), whenever its lanes run dry,
+// so warps whose ops probe long keep fewer ops and all finish close
+// together; `warps` is the launch's warp count.
 template <int SCHEME, bool META, int B, int T, int KIND>
 __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs& a, int upsert_op, bool lockfree,
                                            u64 begin, u64 end, WarpSmem& sm, int lane, u64* ticket = nullptr,
-                                           u64 share = 0) {
+                                           u64 share = 0, u64 warps = 1) {
   using Ops = TileOps<SCHEME, META, B, T>;
   enum { L_EMPTY = 0, L_ACTIVE = 1, L_PARKED = 2 };
   constexpr int NT = 32 / T;
@@ -1693,11 +1694,16 @@ __device__ __forceinline__ int warp_stream(const TableView& tv, const BatchArgs&
     const unsigned empty = __ballot_sync(kAll, state == L_EMPTY);
     if (!exhausted && empty && next >= end) {  // the share is used up: take the next one
       u64 first = 0;
-      if (lane == 0) first = atomicAdd((unsigned long long*)ticket, 1ull) * share;
+      if (lane == 0) first = atomicAdd((unsigned long long*)ticket, (unsigned long long)share);
       first = __shfl_sync(kAll, first, 0);
       if (first < a.n) {
         next = first;
         end = (a.n - first < share) ? a.n : first + share;
+        // guided shares: once fewer than four shares per warp are left, take
+        // a quarter per warp of what is left (a multiple of 32, at least 32),
+        // so that the warps run dry together at the end of the launch
+        const u64 left = ((a.n - end) / (4 * warps) + 31) / 32 * 32;
+        if (left < share) share = left < 32 ? 32 : left;
         if (ring && first + (u64)lane < end) {
           ptx::cp_async8(&sm.in_key[lane], a.keys + (first + lane) * ks);
           if (want_v) ptx::cp_async8(&sm.in_val[lane], a.vals + (first + lane) * ks);
@@ -1941,7 +1947,8 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
   // Work comes from the launch's ticket: warps that draw long probe
   // sequences take less of it.  Shares shrink with the batch so that a small
   // launch still spreads over every warp (about four shares per warp, 32 to
-  // kStreamShare ops each; one to kChunkGroup chunks).
+  // kStreamShare ops each; one to kChunkGroup chunks), and shrink again
+  // towards the end of the launch (guided self-scheduling).
   u64* ticket = &tv.ctr->ticket;
   const u64 warps = (u64)gridDim.x * kWarps;
   if (!tv.stream || lock_bound || rounds) {
@@ -1954,13 +1961,18 @@ __global__ void __launch_bounds__(kThreads, 4) batch_kernel(TableView tv, BatchA
       c0 = __shfl_sync(0xffffffffu, c0, 0);
       if (c0 >= nchunks) break;
       const u64 c1 = (nchunks - c0 < group) ? nchunks : c0 + group;
+      // guided: once fewer than four groups per warp are left, take a
+      // quarter per warp of what is left (at least one chunk)
+      const u64 left = (nchunks - c1) / (4 * warps);
+      if (left < group) group = left < 1 ? 1 : left;
       for (u64 ch = c0; ch < c1; ++ch)
         dcount += warp_chunk<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, ch * 32, s_w[w], lane);
     }
   } else {
     u64 share = (a.n / (4 * warps) + 31) / 32 * 32;
     share = share < 32 ? 32 : (share > kStreamShare ? kStreamShare : share);
-    dcount += warp_stream<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, 0, 0, s_w[w], lane, ticket, share);
+    dcount += warp_stream<SCHEME, META, B, T, KIND>(tv, a, a.op, lockfree, 0, 0, s_w[w], lane, ticket, share,
+                                                    warps);
   }
   if (KIND != KIND_QUERY && KIND != KIND_PROBE) {
     const int mine = __reduce_add_sync(0xffffffffu, dcount);
