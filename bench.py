@@ -9,6 +9,11 @@ prefilled to 0.85 load outside the timed region.  One step, per table:
   erase the slice again (0.90 -> 0.85), read the live count.
 ``value`` = all ops of all tables / device time of K steps (Gops/s); ``e2e``
 times the same steps through the C ABI with pinned host buffers (copies in).
+Unless --no-extra, the line also carries the read-bandwidth probes, the same
+step on 2^22-slot (L2-resident) tables, the batched leg (1024 tables, one
+graph launch vs per-table launches), the serving leg (p50/p99 and Gops/s,
+continuous batching vs per-request launches) and config 3's mixed Zipf
+batches on 2^27-slot tables.
 
 --impl reference: the CPU oracle (the map definition, single thread) on a
 bounded sample of the same step; ``--sweep`` writes the load/tile sweep.
@@ -68,8 +73,8 @@ def parse():
                         "default), inputs and results in place (2), in place for inserts and erases and "
                         "staged otherwise (3)")
     p.add_argument("--no-extra", action="store_true",
-                   help="default line only: skip the read-peak probes, the L2-resident leg and the short "
-                        "batched and serving legs")
+                   help="default line only: skip the read-peak probes, the L2-resident leg, the short "
+                        "batched and serving legs and the config-3 mixed-batch leg")
     p.add_argument("--serve-requests", type=int, default=240, help="requests of the default line's serving leg")
     p.add_argument("--tiles", default="auto", choices=["auto", "paper", "4", "8", "16", "32"],
                    help="auto: per design, the tile size with the fastest step (measured before timing); "
@@ -520,8 +525,11 @@ def bench_ours(args, rank, world, peak_override=None, access_peak=None):
             "tiles": {d[2]: t.info()["tile"] for d, (_, t) in zip(designs, tables)},
             "tile_choice": args.tiles, "tile_tuning_ms_per_step": tuning,
             "bucket_slots": {d[2]: t.info()["bucket_slots"] for d, (_, t) in zip(designs, tables)},
-            "l2": "inputs larger than L2, no flush: each table (4-4.5 GiB, 33x the 129 MB L2) is probed at"
-                  " random; query/upsert key arrays are 134 MB",
+            "l2": (f"inputs larger than L2, no flush: each table ({S * 16 / 2**30:.2f} GiB of slots, "
+                   f"{S * 16 / 129e6:.0f}x the 129 MB L2) is probed at random; query/upsert key arrays are "
+                   f"{nq * 8 / 1e6:.0f} MB") if S * 16 > 129e6 else
+                  (f"L2-resident tables, no flush: {S * 16 / 2**20:.0f} MiB of slots per table, which L2 holds "
+                   f"while the table's phases run; query/upsert key arrays are {nq * 8 / 1e6:.0f} MB"),
             "parallelism": f"replicas x{world}",
         },
         "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "breakdown": breakdown,
@@ -554,10 +562,11 @@ def bench_l2_leg(args, rank, world, peaks):
             if "frac_of_random_line_rate" in d:
                 d["frac_of_l2_random_line_rate"] = d.pop("frac_of_random_line_rate")
             bd[name][ph] = d
+    roof = dict(r["roofline"], bound="l2")
     return {"workload": r["config"]["workload"], "value": r["value"], "unit": UNIT, "steps": r["steps"],
             "ms_per_step": r["ms_per_step"], "l2_peak_gbs": l2_peak, "l2_random_line_gbs": lines,
-            "tiles": r["config"]["tiles"],
-            "roofline": r["roofline"], "clocks": r["clocks"], "breakdown": bd}
+            "tiles": r["config"]["tiles"], "l2": r["config"]["l2"],
+            "roofline": roof, "clocks": r["clocks"], "breakdown": bd}
 
 
 def bench_e2e(args, tables, keys_slice, vals_slice, keys_pos, keys_neg, keys_up, vals_up, base_n, ops_per_step,
@@ -1224,6 +1233,10 @@ def main():
         res["batched"] = bench_batched(args, n_tables=1024, reps=5, tune_reps=1)
         torch.cuda.empty_cache()
         res["serve"] = bench_serve(args, n_req=args.serve_requests, reps=3)
+        torch.cuda.empty_cache()
+        batches = make_mixed_batches()  # spawn-started pool: safe after the GPU context exists
+        res["mixed"] = bench_mixed(args, batches)
+        del batches
         torch.cuda.empty_cache()
     if rank == 0:
         if not args.no_cpu:
