@@ -327,9 +327,9 @@ ws_status ws_batch_plan_destroy(ws_batch_plan* plan);
  * that loads the library, held until exit) instead of allocated memory.
  * Limits: at most 1024 items and 16 distinct phases per call; larger calls
  * return WS_ERR_INVALID and ws_cuda_error_string() says why.  The first call
- * on a device looks up the array's device address (make that call before any
- * stream capture).  Every call reuses the array: calls whose work overlaps on
- * the GPU race, so order them on one stream.  Device pointers only. */
+ * on a device looks up the array's device address.  Every call reuses the
+ * array: calls whose work overlaps on the GPU race, so order them on one
+ * stream.  Device pointers only. */
 ws_status ws_batch_run_noalloc(const ws_batch_item* items, uint64_t n_items, ws_stream stream);
 
 /* ---------------------------------------------------------------------------

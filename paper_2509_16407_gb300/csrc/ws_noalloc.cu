@@ -13,7 +13,7 @@
 // The array (kScratchBytes, about 193 KiB) exists on every GPU that loads
 // the library until the process exits.  Its device address is looked up once
 // per device, on the first call that uses that device (cudaGetSymbolAddress
-// with the device current); make that first call before any stream capture.
+// with the device current).
 // Every call reuses the same array and it keeps the last call's contents:
 // each call rewrites the descriptors it uses and zeroes its work tickets.
 // Calls whose work overlaps on the GPU race on the array -- order them on one
