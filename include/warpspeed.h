@@ -179,7 +179,7 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  buffers that are page-locked and mapped into the device's address space
  *  (cudaHostAlloc / cudaMallocHost / cudaHostRegister memory with unified
  *  addressing).  0: every host buffer is staged through the table's device
- *  chunks (copy engines, four chunk buffers rotating against the kernels).
+ *  chunks (copy engines, eight chunk buffers rotating against the kernels).
  *  1: the kernels read keys, values and op codes in place over the host
  *  link; host result buffers are still staged.  2: results are written in
  *  place too.  3: 1 for insert-if-unique and erase calls (their probe
@@ -197,9 +197,12 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  in place).  Results written in place cost most (scattered small writes
  *  over the host link). */
 /*  WS_OPT_STAGE_CHUNK (16..24, default 22): log2 of the ops per chunk of the
- *  staging pipeline for host buffers (four rotating chunk buffers per table,
- *  allocated at the first host-buffer call; changing the size synchronises
- *  the table's last stream and frees them). */
+ *  staging pipeline for host buffers (eight rotating chunk buffers per table,
+ *  26 bytes per op each: 832 MiB at the default, allocated at the first
+ *  host-buffer call; changing the size synchronises the table's last stream
+ *  and frees them).  The staging copies of every table on a device run on
+ *  one host-to-device and one device-to-host stream of that device, in the
+ *  order the calls were issued. */
 enum { WS_OPT_PRELOAD = 1, WS_OPT_PHASED = 2, WS_OPT_LANE_WAVES = 3, WS_OPT_STREAM = 4, WS_OPT_HOST_DIRECT = 5,
        WS_OPT_STAGE_CHUNK = 6 };
 ws_status ws_set_option(ws_table* t, int option, int64_t value);

@@ -3,7 +3,10 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <utility>
 
 #include "ws_internal.h"
 
@@ -44,9 +47,28 @@ void free_staging(Staging* s) {
     if (s->k_done[b]) cudaEventDestroy(s->k_done[b]);
     if (s->out_done[b]) cudaEventDestroy(s->out_done[b]);
   }
-  if (s->h2d) cudaStreamDestroy(s->h2d);
-  if (s->d2h) cudaStreamDestroy(s->d2h);
-  delete s;
+  delete s;  // the copy streams are the device's, shared by every table
+}
+
+// One H2D and one D2H copy stream per device, shared by every table's
+// staging, so that copies run in the order the calls were issued.
+bool shared_copy_streams(int device, cudaStream_t* h2d, cudaStream_t* d2h) {
+  static std::mutex mu;
+  static std::map<int, std::pair<cudaStream_t, cudaStream_t>> streams;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = streams.find(device);
+  if (it == streams.end()) {
+    cudaStream_t a = nullptr, b = nullptr;
+    if (cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamDestroy(a);
+      return false;
+    }
+    it = streams.emplace(device, std::make_pair(a, b)).first;
+  }
+  *h2d = it->second.first;
+  *d2h = it->second.second;
+  return true;
 }
 
 ws_status free_table_memory(ws_table* t) {
@@ -81,9 +103,7 @@ ws_status ensure_staging(ws_table* t) {
          cudaEventCreateWithFlags(&s->k_done[b], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&s->out_done[b], cudaEventDisableTiming) == cudaSuccess;
   }
-  if (ok)
-    ok = cudaStreamCreateWithFlags(&s->h2d, cudaStreamNonBlocking) == cudaSuccess &&
-         cudaStreamCreateWithFlags(&s->d2h, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok) ok = shared_copy_streams(t->device, &s->h2d, &s->d2h);
   if (!ok) {
     const cudaError_t e = cudaGetLastError();
     free_staging(s);

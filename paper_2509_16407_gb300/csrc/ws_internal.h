@@ -15,9 +15,12 @@ using ws::u32;
 // Staging for host batch buffers: kBufs rotating chunk buffers, H2D copies on
 // one stream, kernels on the caller's stream, D2H copies on a third, chained
 // by events, so the copies of later chunks run while earlier chunks' kernels
-// do.
+// do.  The two copy streams belong to the device and are shared by every
+// table on it, so copies run in the order the calls were issued (with a
+// stream per table, the copies of the tables' next calls all started at
+// once and starved the current call).
 struct Staging {
-  static constexpr int kBufs = 4;
+  static constexpr int kBufs = 8;
   u64 cap = 0;  // ops per chunk
   u64* keys[kBufs] = {};
   u64* vals[kBufs] = {};
