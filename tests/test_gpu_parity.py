@@ -502,6 +502,47 @@ def test_host_direct_matches_oracle(ws, oracle_mod, scheme, meta, mode):
 
 
 # --------------------------------------------------------------------------
+# staging shared by the tables of a device: the staging copies of every
+# table run on the device's two copy streams in call order; calls on every
+# design's table, every buffer staged in 2^16-op chunks, the tables spread
+# over two user streams and their calls interleaved without synchronising,
+# give the oracle's results
+# --------------------------------------------------------------------------
+def test_staging_shared_across_tables_and_streams(ws, oracle_mod):
+    import torch
+    tabs = [ws.Table(1 << 20, scheme, meta) for scheme, meta in DESIGNS]
+    for t in tabs:
+        t.set_host_direct(0)
+        t.set_stage_chunk(16)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).pin_memory()
+    oms = [oracle_mod.OracleMap() for _ in tabs]
+    n = 150000  # three chunks, the last one ragged
+    pending = []
+    for r in range(3):
+        for i, t in enumerate(tabs):
+            s = streams[i % 2]  # calls on one table stay on one stream
+            keys = W.distinct_keys(7000 + 10 * i + r, n, start=r * n)
+            vals = W.splitmix64(7100 + 10 * i + r, n)
+            kb, vb = pin(keys), pin(vals)
+            st = t.insert(kb, vb, return_status=True, stream=s)
+            want_st = oms[i].insert(keys, vals)
+            q = np.concatenate([keys[::2], W.distinct_keys(7200 + 10 * i + r, n // 4, start=10 * n)])
+            qb = pin(q)
+            out = torch.empty(q.size, dtype=torch.int64).pin_memory()
+            _, qs = t.query(qb, out=out, return_status=True, stream=s)
+            want_v, want_q = oms[i].query(q)
+            pending.append((kb, vb, qb, st, want_st, out, qs, want_v, want_q))
+    torch.cuda.synchronize()
+    for kb, vb, qb, st, want_st, out, qs, want_v, want_q in pending:
+        assert (st.numpy() == want_st).all()
+        assert (out.numpy().view(np.uint64) == want_v).all() and (qs.numpy() == want_q).all()
+    for t, om in zip(tabs, oms):
+        assert t.count() == om.count()
+        t.close()
+
+
+# --------------------------------------------------------------------------
 # work tickets: every single-table launch takes its work from a per-table
 # ticket that the launch's last block returns to zero; back-to-back launches
 # of sizes around a share (1 op ... a few shares, streaming and chunked
