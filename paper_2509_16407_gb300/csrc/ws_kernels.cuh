@@ -1415,6 +1415,10 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
             if (q < nr) ptx::cp_async16(&sm.pre.flat(q, lane), tv.slots + sm.bw[sm.list[r0 + q]] * 32 + (u64)lane);
           ptx::cp_async_wait_all();
           __syncwarp();
+          // the votes of bucket q go to the lane owning its op; the owners
+          // then settle their snapshots together, not one after another
+          unsigned own_k = 0, own_f = 0;
+          int own_q = -1;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             if (q >= nr) break;  // warp-uniform
@@ -1422,18 +1426,21 @@ __device__ __forceinline__ int warp_chunk(const TableView& tv, const BatchArgs& 
             const u64 k = sm.pre.flat(q, lane).key;
             const unsigned mk = __ballot_sync(0xffffffffu, k == sm.key[j]);
             const unsigned mf = __ballot_sync(0xffffffffu, k == KEY_EMPTY || k == KEY_TOMB);
-            if (lane == j) {
-              occ = 32u - (u32)__popc(mf);
-              if (mk) {
-                hs = __ffs(mk) - 1;
-                hv = sm.pre.flat(q, hs).val;
-              }
-              if (mf) {
-                fs = __ffs(mf) - 1;
-                const Slot f = sm.pre.flat(q, fs);
-                fk = f.key;
-                fv = f.val;
-              }
+            own_k = lane == j ? mk : own_k;
+            own_f = lane == j ? mf : own_f;
+            own_q = lane == j ? q : own_q;
+          }
+          if (own_q >= 0) {
+            occ = 32u - (u32)__popc(own_f);
+            if (own_k) {
+              hs = __ffs(own_k) - 1;
+              hv = sm.pre.flat(own_q, hs).val;
+            }
+            if (own_f) {
+              fs = __ffs(own_f) - 1;
+              const Slot f = sm.pre.flat(own_q, fs);
+              fk = f.key;
+              fv = f.val;
             }
           }
           __syncwarp();  // the next round overwrites the rows
