@@ -159,7 +159,8 @@ ws_status ws_set_spin_limit(ws_table* t, uint32_t spins);
  *  keys); otherwise results are undefined. */
 /*  WS_OPT_STREAM (default 1): single-table calls run "streaming lanes": each
  *  warp serves shares of the batch taken from a per-launch work ticket (so
- *  warps whose ops probe long take fewer), a lane follows its op's probe
+ *  warps whose ops probe long take fewer; the shares shrink towards the end
+ *  of the launch so the warps run dry together), a lane follows its op's probe
  *  sequence one bucket per wave and takes the next op as soon as its op
  *  settles; ops the lanes cannot settle go to the tiles.  0 serves 32-op
  *  chunks (lane waves, then tiles for what is left), as batched and serving
